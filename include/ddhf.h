@@ -1,0 +1,275 @@
+/*
+ * ddhf.h - C ABI of the GB300 DDHF hot path (libddhf.so).
+ *
+ * DDHF ("Real-Time Drone Detection in Event Cameras via Per-Pixel Frequency
+ * Analysis", arXiv 2603.08386) detects drone rotors in an event-camera stream:
+ * the events of a window are binned per pixel (Sec. 3.5), each active pixel's
+ * non-uniform DFT power spectrum is evaluated directly (Sec. 3.3, Eq. 6),
+ * noise-like spectra are rejected by spectral flatness (Sec. 3.4, Eq. 7), a
+ * median-normalised harmonic comb picks rotor pixels and their dominant
+ * frequency (Eq. 8-11), and the rotor mask becomes drone boxes by 8-connected
+ * labelling, an area filter and centroid merging (Sec. 3.5, Eq. 12).
+ *
+ * Conventions for every entry point:
+ *  - Data pointers are CUDA device pointers owned by the caller unless a
+ *    parameter says "host". The library never frees or retains them past the
+ *    call (except the per-window event lists it copies into its workspace).
+ *  - Work is enqueued asynchronously on `stream` (a cudaStream_t; NULL is the
+ *    legacy default stream). Counts that depend on the data (events kept,
+ *    active pixels, boxes) are written to device memory, so a sequence of
+ *    calls can be captured into a CUDA graph; ddhf_get_stats() synchronises
+ *    and reads them back on the host.
+ *  - No call aborts or throws. Each returns a ddhf_status; on failure
+ *    ddhf_last_error(ctx) holds a one-line message. Invalid events (outside
+ *    the window or the sensor, bad polarity) are dropped and counted, not
+ *    errors. Overflow of a caller-sized output is flagged on the device and
+ *    reported as DDHF_ERR_CAPACITY by ddhf_get_stats().
+ *  - A context is bound to the CUDA device that was current at ddhf_create()
+ *    and must be used from one host thread at a time.
+ */
+#ifndef DDHF_H
+#define DDHF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ddhf_ctx ddhf_ctx;
+typedef void *ddhf_stream; /* cudaStream_t */
+
+typedef enum {
+  DDHF_OK = 0,
+  DDHF_ERR_INVALID_ARG = 1, /* a pointer, size or parameter is out of range */
+  DDHF_ERR_CUDA = 2,        /* a CUDA runtime call failed (message in last_error) */
+  DDHF_ERR_CAPACITY = 3,    /* an output or workspace was too small */
+  DDHF_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+  DDHF_ERR_UNSUPPORTED = 5, /* a configuration this build does not handle */
+  DDHF_ERR_STATE = 6        /* calls out of order (e.g. spectrum before binning) */
+} ddhf_status;
+
+/* Frequency grid (Sec. 3.3 Eq. 6, Sec. 3.5): bin j = 0..n_bins-1 evaluates
+ * a_j = a0 + j*da in units of 1/denom cycles per microsecond, so the phase of
+ * an event at tau microseconds is the exact integer residue (a_j*tau) mod
+ * denom in units of 1/denom cycles.
+ *   Hz grid:   a_j in mHz, denom = 1e9 (f_j = a_j/1000 Hz).
+ *   Mode grid: a0 = 0, da = 1, denom = window_us: the paper's integer modes
+ *              k = 0..K-1 over timestamps normalised to the window.
+ * Requires a0 >= 0, da > 0, 0 < denom < 2^31, n_bins in [1, 16384] and
+ * a_{n_bins-1} < 2^32. */
+typedef struct {
+  int64_t a0;
+  int64_t da;
+  int64_t denom;
+  int32_t n_bins;
+  int32_t reserved;
+} ddhf_grid;
+
+/* Thresholds of Sec. 3.4-3.5; ddhf_default_params() gives Table 2's final
+ * values (0.89, 1.5, 4, 3, 4, 6, 147, 19.05). d is Table 2's Delta k (the
+ * harmonic half-width d_k of Eq. 8, in bins). polarity_01 = 1 accepts
+ * polarities {0, 1} (0 meaning -1) instead of {-1, +1}.
+ * Requires M >= 1, 0 <= d, 1 <= h_min, n_min >= 1, A_min >= 0, alpha >= 0 and
+ * M*(2d+1) <= 254. */
+typedef struct {
+  float tau_sf;
+  float tau_comb;
+  int32_t M;
+  int32_t d;
+  int32_t h_min;
+  int32_t n_min;
+  int32_t A_min;
+  int32_t polarity_01;
+  double alpha;
+} ddhf_params;
+
+/* One detection (Sec. 3.5): inclusive pixel bounds and the number of rotor
+ * pixels of the merged components. */
+typedef struct {
+  int32_t x0, y0, x1, y1, n_px;
+} ddhf_box;
+
+/* One window of one event stream for the batched call. Event arrays are
+ * device pointers, n events each: x, y int16 pixel coordinates, t_us int64
+ * microseconds, p int8 polarity. */
+typedef struct {
+  const int16_t *x;
+  const int16_t *y;
+  const int64_t *t_us;
+  const int8_t *p;
+  int64_t n;
+  int64_t t0_us;
+  int64_t window_us;
+} ddhf_window;
+
+/* Counters of the last binned window (slot 0) and of the last detection. */
+typedef struct {
+  int64_t n_in;         /* events passed to the last binning call */
+  int64_t n_valid;      /* events kept */
+  int64_t n_dropped;    /* events outside the window/sensor or bad polarity */
+  int64_t n_active;     /* pixels with at least n_min events */
+  int64_t n_rotor;      /* rotor-mask pixels of the last detection */
+  int64_t n_boxes;      /* boxes of the last detection (may exceed cap) */
+  int64_t terms;        /* sum over active pixels of count * n_bins */
+  int64_t graph_kernels;/* kernel nodes of the last captured ddhf_detect_batch graph */
+  uint32_t device_flags;/* DDHF_FLAG_* bits raised on the device */
+  uint32_t reserved;
+} ddhf_stats;
+
+#define DDHF_FLAG_CAPACITY 1u /* a caller-sized output overflowed */
+#define DDHF_FLAG_TIMEOUT 2u  /* a bounded device-side loop hit its limit */
+#define DDHF_FLAG_INTERNAL 4u /* an internal consistency check failed (reported as DDHF_ERR_CUDA) */
+
+/* NDFT evaluation forms for ddhf_power_spectrum (Eq. 6; all give P_j in FP32).
+ *  SINCOS   one warp per pixel, lanes own bins; exact integer phase per term,
+ *           advanced by an exact modular step, then FP32 sin/cos per term.
+ *  RECUR    one warp per pixel; each lane rotates its bins by an exact
+ *           per-event step phasor, re-seeded exactly every 32 bins.
+ *  BLOCKED  persistent kernel: F[32b + r] = sum_k A[b][k] B[k][r] with exact
+ *           seeds A = p e^{-2 pi i a_{32b} tau} and rotations B = u^r, as a
+ *           three-multiplication complex product per term; heavy pixels are
+ *           split over a thread block. The form used by ddhf_detect.
+ *  NAIVE32  precision study only: FP32 phase 2 pi f t from the absolute time.
+ *  KAHAN    SINCOS with compensated (Kahan) accumulation.
+ *  F64      check path: FP64 phase and accumulation on the GPU. */
+#define DDHF_FORM_SINCOS 0
+#define DDHF_FORM_RECUR 1
+#define DDHF_FORM_BLOCKED 2
+#define DDHF_FORM_NAIVE32 3
+#define DDHF_FORM_KAHAN 4
+#define DDHF_FORM_F64 5
+
+/* Launch tuning of the persistent BLOCKED kernel (chosen by the autotuner).
+ *  heavy_min   pixels with at least this many events are processed by a
+ *              whole thread block (events split over its warps), the others
+ *              by one warp each;
+ *  warps_per_block  warps per thread block (2, 4 or 8);
+ *  blocks_per_sm    resident blocks per SM used to size the persistent grid. */
+typedef struct {
+  int32_t heavy_min;
+  int32_t warps_per_block;
+  int32_t blocks_per_sm;
+  int32_t reserved;
+} ddhf_tuning;
+
+const char *ddhf_status_string(ddhf_status s);
+
+/* Table 2 final values. out: host pointer. */
+ddhf_status ddhf_default_params(ddhf_params *out);
+
+/* Create a context for a W x H sensor (1 <= W, H <= 32767, W*H <= 2^26) and
+ * one frequency grid. Allocates device workspace on the current device for
+ * up to max_windows windows of at most max_events events each (binning
+ * scratch, per-window pixel lists, masks, labels, work queues). grid and
+ * params are host pointers and are copied. *out receives the context. */
+ddhf_status ddhf_create(int32_t W, int32_t H, const ddhf_grid *grid,
+                        const ddhf_params *params, int64_t max_events,
+                        int32_t max_windows, ddhf_ctx **out);
+
+/* Release the context and its device workspace (synchronises the device). */
+ddhf_status ddhf_destroy(ddhf_ctx *ctx);
+
+ddhf_status ddhf_set_tuning(ddhf_ctx *ctx, const ddhf_tuning *tuning);
+ddhf_status ddhf_get_tuning(const ddhf_ctx *ctx, ddhf_tuning *out);
+
+/* Sec. 3.5 "Event processing": keep events with t0 <= t < t0+window_us,
+ * 0 <= x < W, 0 <= y < H and a valid polarity, sort them stably by pixel key
+ * y*W + x into the context's per-pixel list (slot 0), and list the active
+ * pixels (at least n_min events) in ascending key order. n may be 0.
+ * Requires n <= max_events and window_us < 2^31. */
+ddhf_status ddhf_bin_events(ddhf_ctx *ctx, const int16_t *x, const int16_t *y,
+                            const int64_t *t_us, const int8_t *p, int64_t n,
+                            int64_t t0_us, int64_t window_us, ddhf_stream stream);
+
+/* Copy the per-pixel list of slot 0 out of the context:
+ *   offsets [W*H+1] uint32: events of pixel k are ev[offsets[k] .. offsets[k+1])
+ *   ev      [cap_ev] uint32: bits 0-30 tau = t - t0 (us), bit 31 set for p = -1
+ *   active  [W*H]   uint32: active pixel keys, ascending (n_active entries)
+ *   counts  [4]     int64:  n_valid, n_dropped, n_active, n_in
+ * Any pointer may be NULL to skip it. Overflow of cap_ev raises
+ * DDHF_FLAG_CAPACITY and copies cap_ev events. */
+ddhf_status ddhf_export_csr(ddhf_ctx *ctx, uint32_t *offsets, uint32_t *ev,
+                            int64_t cap_ev, uint32_t *active, int64_t *counts,
+                            ddhf_stream stream);
+
+/* Eq. 6 and P_j = |F_j|^2 for every active pixel of slot 0, in active-list
+ * order: P[a*n_bins + j] (FP32, row a of the a-th active pixel). `form` is a
+ * DDHF_FORM_*. Rows beyond cap_px are not written (DDHF_FLAG_CAPACITY). */
+ddhf_status ddhf_power_spectrum(ddhf_ctx *ctx, int32_t form, float *P, int64_t cap_px,
+                                ddhf_stream stream);
+
+/* Eq. 7-11 on spectra P laid out as ddhf_power_spectrum writes them (rows in
+ * active-list order of slot 0). Per active pixel a: log_sf[a] = ln SF;
+ * snr[a] = max_w SNR_M(w) and f0_bin[a] = its first maximising bin w when
+ * SF <= tau_sf (else 0 and -1); mask[W*H] (uint8, zeroed by the call) gets 1
+ * at rotor pixels (SF <= tau_sf and snr >= tau_comb). log_sf, snr and f0_bin
+ * may be NULL. Given the same P, every output is bit-reproducible. */
+ddhf_status ddhf_comb_score(ddhf_ctx *ctx, const float *P, int64_t cap_px, float *log_sf,
+                            float *snr, int32_t *f0_bin, uint8_t *mask,
+                            ddhf_stream stream);
+
+/* Sec. 3.5 "Segmentation mask processing": 8-connected labels of mask[W*H]
+ * (nonzero = rotor); labels[k] = smallest linear index of k's component,
+ * -1 for background. */
+ddhf_status ddhf_label(ddhf_ctx *ctx, const uint8_t *mask, int32_t *labels,
+                       ddhf_stream stream);
+
+/* Boxes of the components of labels[W*H] (as ddhf_label writes them), boxes
+ * with area (x1-x0+1)(y1-y0+1) < A_min removed, then Eq. 12 centroid merging
+ * repeated until no pair is within alpha * max(w1,h1,w2,h2); merged boxes are
+ * union boxes. Output sorted by (y0, x0, y1, x1, n_px) into boxes[cap];
+ * *n_boxes_dev (device int32) gets the total count, which may exceed cap. */
+ddhf_status ddhf_boxes(ddhf_ctx *ctx, const int32_t *labels, ddhf_box *boxes, int32_t cap,
+                       int32_t *n_boxes_dev, ddhf_stream stream);
+
+/* The whole per-window pipeline of Sec. 3.5 on one window: binning, the
+ * BLOCKED NDFT with SF and comb scoring fused into it (spectra stay on chip),
+ * labelling and boxes. mask_out[W*H] (nullable) receives the rotor mask. */
+ddhf_status ddhf_detect(ddhf_ctx *ctx, const int16_t *x, const int16_t *y,
+                        const int64_t *t_us, const int8_t *p, int64_t n, int64_t t0_us,
+                        int64_t window_us, ddhf_box *boxes, int32_t cap,
+                        int32_t *n_boxes_dev, uint8_t *mask_out, ddhf_stream stream);
+
+/* ddhf_detect over n_windows windows (windows is a host array) in one
+ * sequence of launches: every window is binned into its own slot, one
+ * persistent BLOCKED kernel scores the pixels of all windows (heavy pixels
+ * first), then labelling and boxes run per window. boxes is [n_windows*cap]
+ * (window w at boxes + w*cap), n_boxes_dev[n_windows], masks_out
+ * [n_windows*W*H] (nullable). Requires n_windows <= max_windows. When
+ * use_graph is nonzero the launch sequence is captured once into a CUDA
+ * graph, keyed by the argument values, and replayed on later calls with the
+ * same arguments. */
+ddhf_status ddhf_detect_batch(ddhf_ctx *ctx, const ddhf_window *windows, int32_t n_windows,
+                              ddhf_box *boxes, int32_t cap, int32_t *n_boxes_dev,
+                              uint8_t *masks_out, int32_t use_graph, ddhf_stream stream);
+
+/* Per-pixel outputs of slot w of the last ddhf_detect / ddhf_detect_batch:
+ * active [W*H] uint32 keys, log_sf, snr [W*H] float, f0_bin [W*H] int32 in
+ * active-list order, counts [4] as in ddhf_export_csr. Nullable. */
+ddhf_status ddhf_export_scores(ddhf_ctx *ctx, int32_t slot, uint32_t *active, float *log_sf,
+                               float *snr, int32_t *f0_bin, int64_t *counts,
+                               ddhf_stream stream);
+
+/* Tracing: when enable is nonzero, CUDA events bracket the three stages of
+ * every later ddhf_detect / ddhf_detect_batch call (also inside a captured
+ * graph; enabling or disabling drops a cached graph). ddhf_stage_times()
+ * waits for the last recorded call and writes out_ms[3] (host) = device time
+ * of {binning of all windows, fused NDFT + SF + comb kernel, labels + boxes}
+ * in milliseconds. Returns DDHF_ERR_STATE if nothing was recorded. */
+ddhf_status ddhf_enable_stage_timing(ddhf_ctx *ctx, int32_t enable);
+ddhf_status ddhf_stage_times(ddhf_ctx *ctx, float *out_ms);
+
+/* Synchronise the context's last stream and read its counters and device
+ * flags. Returns DDHF_ERR_CAPACITY / DDHF_ERR_TIMEOUT when the matching
+ * flag is set (the stats are filled either way); the flags are then cleared. */
+ddhf_status ddhf_get_stats(ddhf_ctx *ctx, ddhf_stats *out);
+
+/* One-line description of the last failure of this context ("" if none). */
+const char *ddhf_last_error(const ddhf_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DDHF_H */

@@ -1,0 +1,380 @@
+// Event binning (Sec. 3.5 "Event processing"): window + validity filter, a
+// stable sort of the events by pixel key y*W + x into a per-pixel list, and
+// the list of active pixels (at least n_min events, Table 2).
+//
+// Design: least-significant-digit radix sort over the key bits in 1-3 passes
+// of <= 11 bits. Each pass is reduce-then-scan: a histogram kernel writes one
+// count per (digit, chunk of 8192 events) in digit-major order, an exclusive
+// scan of that table gives every (digit, chunk) its output offset, and a
+// scatter kernel re-reads its chunk and places each element at
+// offset + (its rank among equal digits earlier in the chunk). The in-chunk
+// rank is computed warp by warp with __match_any_sync and per-warp digit
+// counters in shared memory, so element order inside a digit is input order
+// and every pass is stable; no block waits on another block. The first pass
+// reads the raw (x, y, t, p) arrays directly and packs each kept event into
+// one 32-bit word: tau = t - t0 in bits 0-30, bit 31 set for polarity -1.
+// Per-pixel counts come from segment boundaries of the sorted keys, and one
+// 64-bit scan of (count << 32 | active flag) gives both the CSR offsets and
+// the active-pixel list.
+#include "ddhf_internal.cuh"
+
+namespace ddhf {
+
+namespace {
+
+struct RawIn {
+  const int16_t *x, *y;
+  const int64_t *t;
+  const int8_t *p;
+  int64_t n;
+  int64_t t0;
+  uint64_t win;
+  int W, H, pol01;
+};
+
+__device__ __forceinline__ bool load_raw(const RawIn &in, int64_t e, uint32_t &key,
+                                         uint32_t &val) {
+  int xx = in.x[e], yy = in.y[e];
+  int64_t tt = in.t[e];
+  int pp = in.p[e];
+  bool okp = in.pol01 ? (pp == 0 || pp == 1) : (pp == 1 || pp == -1);
+  bool neg = in.pol01 ? (pp == 0) : (pp == -1);
+  uint64_t dt = (uint64_t)tt - (uint64_t)in.t0;
+  bool ok = okp && xx >= 0 && xx < in.W && yy >= 0 && yy < in.H && tt >= in.t0 && dt < in.win;
+  key = (uint32_t)(yy * in.W + xx);
+  val = (uint32_t)dt | (neg ? kSignBit : 0u);
+  return ok;
+}
+
+template <bool RAW>
+__global__ void __launch_bounds__(kBinThreads) k_hist(RawIn raw, const uint32_t *__restrict__ kin,
+                                                      const uint32_t *__restrict__ n_dev,
+                                                      uint32_t *__restrict__ hist, int64_t nchunks,
+                                                      int shift, int nb) {
+  __shared__ uint32_t sh[1 << kMaxDigitBits];
+  const int64_t n = RAW ? raw.n : (int64_t)*n_dev;
+  const int64_t chunk = blockIdx.x;
+  const int64_t c0 = chunk * kBinChunk;
+  for (int d = threadIdx.x; d < nb; d += blockDim.x) sh[d] = 0;
+  __syncthreads();
+  const int64_t c1 = min(n, c0 + (int64_t)kBinChunk);
+  const uint32_t lane = threadIdx.x & 31;
+  for (int64_t base = c0; base < c1; base += blockDim.x) {
+    int64_t e = base + threadIdx.x;
+    uint32_t d = (uint32_t)nb;  // sentinel: not counted
+    if (e < c1) {
+      uint32_t key, val;
+      if (RAW) {
+        if (load_raw(raw, e, key, val)) d = (key >> shift) & (uint32_t)(nb - 1);
+      } else {
+        d = (kin[e] >> shift) & (uint32_t)(nb - 1);
+      }
+    }
+    uint32_t peers = __match_any_sync(0xffffffffu, d);
+    if (d < (uint32_t)nb && __popc(peers & ((1u << lane) - 1)) == 0)
+      atomicAdd(&sh[d], (uint32_t)__popc(peers));
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < nb; d += blockDim.x) hist[(int64_t)d * nchunks + chunk] = sh[d];
+}
+
+template <bool RAW>
+__global__ void __launch_bounds__(kBinThreads) k_scatter(
+    RawIn raw, const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin,
+    const uint32_t *__restrict__ n_dev, uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
+    const uint32_t *__restrict__ hscan, int64_t nchunks, int shift, int nb) {
+  extern __shared__ uint32_t sm[];
+  const int stride = nb + 1;
+  uint32_t *wcnt = sm;                       // [8][nb + 1] per-warp counts this round
+  uint32_t *run = wcnt + 8 * stride;         // [nb + 1] counts of earlier rounds
+  uint32_t *base = run + stride;             // [nb] global offset of (digit, chunk)
+  const int64_t n = RAW ? raw.n : (int64_t)*n_dev;
+  const int64_t chunk = blockIdx.x;
+  const int64_t c0 = chunk * kBinChunk;
+  if (c0 >= n) return;
+  for (int i = threadIdx.x; i < 9 * stride; i += blockDim.x) sm[i] = 0;
+  for (int d = threadIdx.x; d < nb; d += blockDim.x) base[d] = hscan[(int64_t)d * nchunks + chunk];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1;
+  uint32_t *my = wcnt + warp * stride;
+  for (int r = 0; r < kBinRounds; ++r) {
+    uint32_t dg[kBinItems], kk[kBinItems], vv[kBinItems], rk[kBinItems];
+#pragma unroll
+    for (int i = 0; i < kBinItems; ++i) {
+      int64_t e = c0 + (int64_t)r * (kBinThreads * kBinItems) + warp * (32 * kBinItems) + i * 32 +
+                  lane;
+      uint32_t d = (uint32_t)nb, key = 0, val = 0;
+      if (e < n) {
+        if (RAW) {
+          if (load_raw(raw, e, key, val)) d = (key >> shift) & (uint32_t)(nb - 1);
+        } else {
+          key = kin[e];
+          val = vin[e];
+          d = (key >> shift) & (uint32_t)(nb - 1);
+        }
+      }
+      uint32_t peers = __match_any_sync(0xffffffffu, d);
+      uint32_t before = __popc(peers & lt);
+      uint32_t cnt = my[d];
+      __syncwarp();
+      if (before == 0) my[d] = cnt + __popc(peers);
+      __syncwarp();
+      dg[i] = d;
+      kk[i] = key;
+      vv[i] = val;
+      rk[i] = cnt + before;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kBinItems; ++i) {
+      uint32_t d = dg[i];
+      if (d < (uint32_t)nb) {
+        uint32_t pre = run[d] + rk[i];
+        for (int w2 = 0; w2 < warp; ++w2) pre += wcnt[w2 * stride + d];
+        uint32_t dest = base[d] + pre;
+        kout[dest] = kk[i];
+        vout[dest] = vv[i];
+      }
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < stride; d += blockDim.x) {
+      uint32_t s = 0;
+#pragma unroll
+      for (int w2 = 0; w2 < 8; ++w2) {
+        s += wcnt[w2 * stride + d];
+        wcnt[w2 * stride + d] = 0;
+      }
+      run[d] += s;
+    }
+    __syncthreads();
+  }
+}
+
+// Segment bounds of the sorted keys: seg_lo[k] = first index, seg_hi[k] = one
+// past the last index of key k (both 0 for absent keys).
+__global__ void k_seg(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ n_dev,
+                      uint32_t *__restrict__ seg_lo, uint32_t *__restrict__ seg_hi) {
+  const int64_t n = *n_dev;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t k = keys[i];
+    if (i == 0 || keys[i - 1] != k) seg_lo[k] = (uint32_t)i;
+    if (i == n - 1 || keys[i + 1] != k) seg_hi[k] = (uint32_t)(i + 1);
+  }
+}
+
+__global__ void k_pack(const uint32_t *__restrict__ seg_lo, const uint32_t *__restrict__ seg_hi,
+                       uint64_t *__restrict__ packed, int64_t npx, int n_min) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k <= npx;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t v = 0;
+    if (k < npx) {
+      uint32_t cnt = seg_hi[k] - seg_lo[k];
+      v = ((uint64_t)cnt << 32) | (cnt >= (uint32_t)n_min ? 1u : 0u);
+    }
+    packed[k] = v;
+  }
+}
+
+__global__ void k_finish(const uint64_t *__restrict__ scanned, const uint32_t *__restrict__ seg_lo,
+                         const uint32_t *__restrict__ seg_hi, uint32_t *__restrict__ offsets,
+                         uint32_t *__restrict__ active, uint64_t *__restrict__ counters,
+                         int64_t npx, int n_min, int heavy_min, int64_t n_in, int64_t n_bins,
+                         uint64_t *__restrict__ heavy_list, uint32_t *heavy_count,
+                         uint32_t slot, int64_t heavy_cap, uint32_t *flags) {
+  uint64_t terms = 0;
+  uint32_t heavy = 0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k <= npx;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t v = scanned[k];
+    offsets[k] = (uint32_t)(v >> 32);
+    if (k < npx) {
+      uint32_t cnt = seg_hi[k] - seg_lo[k];
+      if (cnt >= (uint32_t)n_min) {
+        active[(uint32_t)v] = (uint32_t)k;
+        terms += (uint64_t)cnt * (uint64_t)n_bins;
+        if (cnt >= (uint32_t)heavy_min) {
+          heavy += 1u;
+          const uint32_t pos = atomicAdd(heavy_count, 1u);
+          if ((int64_t)pos < heavy_cap)
+            heavy_list[pos] = ((uint64_t)slot << 32) | (uint32_t)v;
+          else
+            atomicOr(flags, DDHF_FLAG_CAPACITY);
+        }
+      }
+    } else {
+      counters[0] = v >> 32;                       // n_valid
+      counters[1] = (uint64_t)n_in - (v >> 32);    // n_dropped
+      counters[2] = (uint32_t)v;                   // n_active
+      counters[3] = (uint64_t)n_in;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    terms += __shfl_xor_sync(0xffffffffu, terms, o);
+    heavy += __shfl_xor_sync(0xffffffffu, heavy, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (terms) atomicAdd((unsigned long long *)&counters[5], (unsigned long long)terms);
+    if (heavy) atomicAdd((unsigned long long *)&counters[4], (unsigned long long)heavy);
+  }
+}
+
+// ------------------------------------------------------------------ scans
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+template <typename T>
+__device__ T block_exclusive_scan(T v, T *warp_sums, T &total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T inc = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    T u = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += u;
+  }
+  if (lane == 31) warp_sums[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    T s = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : T(0);
+    T si = s;
+    for (int o = 1; o < 32; o <<= 1) {
+      T u = __shfl_up_sync(0xffffffffu, si, o);
+      if (lane >= o) si += u;
+    }
+    warp_sums[lane] = si - s;  // exclusive per warp
+    if (lane == 31) warp_sums[32] = si;
+  }
+  __syncthreads();
+  total = warp_sums[32];
+  return inc - v + warp_sums[warp];
+}
+
+// Exclusive scan of each tile; tile totals go to part[blockIdx.x]. In place is allowed.
+template <typename T>
+__global__ void __launch_bounds__(kScanThreads) k_scan_tile(const T *in, T *out, T *part, int64_t n) {
+  __shared__ T ws[33];
+  const int64_t t0 = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  T v[kScanItems];
+  T s = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    v[i] = (t0 + i < n) ? in[t0 + i] : T(0);
+    s += v[i];
+  }
+  T total;
+  T ex = block_exclusive_scan<T>(s, ws, total);
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    if (t0 + i < n) out[t0 + i] = ex;
+    ex += v[i];
+  }
+  if (threadIdx.x == 0 && part) part[blockIdx.x] = total;
+}
+
+template <typename T>
+__global__ void k_scan_add(T *out, const T *part, int64_t n) {
+  const T add = part[blockIdx.x];
+  const int64_t t0 = (int64_t)blockIdx.x * kScanTile;
+  for (int i = threadIdx.x; i < kScanTile; i += blockDim.x)
+    if (t0 + i < n) out[t0 + i] += add;
+}
+
+// Recursive exclusive scan; scratch holds the per-level partials and, when
+// total is not null, the grand total is written there.
+template <typename T>
+cudaError_t scan_rec(const T *in, T *out, int64_t n, T *scratch, T *total, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  int64_t nt = ceil_div(n, kScanTile);
+  k_scan_tile<T><<<(unsigned)nt, kScanThreads, 0, s>>>(in, out, nt > 1 ? scratch : total, n);
+  if (nt > 1) {
+    cudaError_t e = scan_rec<T>(scratch, scratch, nt, scratch + nt, total, s);
+    if (e != cudaSuccess) return e;
+    k_scan_add<T><<<(unsigned)nt, 256, 0, s>>>(out, scratch, n);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// Exclusive scan of a uint32 array (in place allowed) using the context scratch.
+ddhf_status launch_scan_u32(Ctx *c, const uint32_t *in, uint32_t *out, int64_t n, cudaStream_t s) {
+  DDHF_CUDA_TRY(c, scan_rec<uint32_t>(in, out, n, c->scan_part, nullptr, s));
+  return DDHF_OK;
+}
+
+ddhf_status bin_window(Ctx *c, int slot_i, const int16_t *x, const int16_t *y, const int64_t *t,
+                       const int8_t *p, int64_t n, int64_t t0, int64_t win, cudaStream_t s) {
+  Slot &sl = c->slots[slot_i];
+  sl.t0 = t0;
+  sl.window_us = win;
+  const int64_t npx = c->npx;
+  uint32_t *ntot = reinterpret_cast<uint32_t *>(c->qctl + 8);  // n_valid of this binning
+  DDHF_CUDA_TRY(c, cudaMemsetAsync(ntot, 0, sizeof(uint32_t), s));
+  DDHF_CUDA_TRY(c, cudaMemsetAsync(sl.counters, 0, 7 * sizeof(uint64_t), s));
+  RawIn raw{x, y, t, p, n, t0, (uint64_t)win, c->W, c->H, c->params.polarity_01};
+  const int64_t nch = ceil_div(n, kBinChunk);
+  uint32_t *kbuf[2] = {c->keysA, c->keysB};
+  uint32_t *vbuf[2] = {c->valsA, c->valsB};
+  int shift = 0;
+  if (nch > 0) {
+    for (int pass = 0; pass < c->npass; ++pass) {
+      const int bits = c->digit_bits[pass];
+      const int nb = 1 << bits;
+      const bool last = pass == c->npass - 1;
+      uint32_t *ko = kbuf[pass & 1];
+      uint32_t *vo = last ? sl.ev : vbuf[pass & 1];
+      const uint32_t *ki = pass ? kbuf[(pass - 1) & 1] : nullptr;
+      const uint32_t *vi = pass ? vbuf[(pass - 1) & 1] : nullptr;
+      const size_t smem = (size_t)(9 * (nb + 1) + nb) * sizeof(uint32_t);
+      if (pass == 0) {
+        k_hist<true><<<(unsigned)nch, kBinThreads, 0, s>>>(raw, nullptr, nullptr, c->hist, nch,
+                                                           shift, nb);
+      } else {
+        k_hist<false><<<(unsigned)nch, kBinThreads, 0, s>>>(raw, ki, ntot, c->hist, nch, shift,
+                                                            nb);
+      }
+      DDHF_CUDA_TRY(c, cudaGetLastError());
+      // pass 0: the grand total of the table is the number of kept events
+      DDHF_CUDA_TRY(c, scan_rec<uint32_t>(c->hist, c->hist, (int64_t)nb * nch, c->scan_part,
+                                          pass == 0 ? ntot : nullptr, s));
+      if (pass == 0) {
+        k_scatter<true><<<(unsigned)nch, kBinThreads, smem, s>>>(raw, nullptr, nullptr, nullptr, ko,
+                                                                 vo, c->hist, nch, shift, nb);
+      } else {
+        k_scatter<false><<<(unsigned)nch, kBinThreads, smem, s>>>(raw, ki, vi, ntot, ko, vo,
+                                                                  c->hist, nch, shift, nb);
+      }
+      DDHF_CUDA_TRY(c, cudaGetLastError());
+      shift += bits;
+    }
+  }
+  const uint32_t *kfinal = kbuf[(c->npass - 1) & 1];
+  DDHF_CUDA_TRY(c, cudaMemsetAsync(c->seg_lo, 0, npx * sizeof(uint32_t), s));
+  DDHF_CUDA_TRY(c, cudaMemsetAsync(c->seg_hi, 0, npx * sizeof(uint32_t), s));
+  const int sm_blocks = c->num_sms * 8;
+  if (nch > 0) {
+    k_seg<<<sm_blocks, 256, 0, s>>>(kfinal, ntot, c->seg_lo, c->seg_hi);
+    DDHF_CUDA_TRY(c, cudaGetLastError());
+  }
+  unsigned pb = (unsigned)std::min<int64_t>(ceil_div(npx + 1, 256), sm_blocks);
+  k_pack<<<pb, 256, 0, s>>>(c->seg_lo, c->seg_hi, c->packed, npx, c->params.n_min);
+  DDHF_CUDA_TRY(c, cudaGetLastError());
+  DDHF_CUDA_TRY(c, scan_rec<uint64_t>(c->packed, c->packed, npx + 1,
+                                      reinterpret_cast<uint64_t *>(c->scan_part), nullptr, s));
+  k_finish<<<pb, 256, 0, s>>>(c->packed, c->seg_lo, c->seg_hi, sl.offsets, sl.active,
+                              sl.counters, npx, c->params.n_min, c->tuning.heavy_min, n,
+                              c->grid.n_bins, c->work, c->qctl, (uint32_t)slot_i, c->heavy_cap,
+                              c->flags);
+  DDHF_CUDA_TRY(c, cudaGetLastError());
+  return DDHF_OK;
+}
+
+void set_bin_attributes() {
+  const int smem = (9 * ((1 << kMaxDigitBits) + 1) + (1 << kMaxDigitBits)) * sizeof(uint32_t);
+  cudaFuncSetAttribute(k_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+}  // namespace ddhf

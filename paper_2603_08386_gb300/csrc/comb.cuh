@@ -1,0 +1,391 @@
+// Warp-level spectral flatness and median-normalised harmonic comb (Sec. 3.4,
+// Eq. 7-11) on one pixel's power spectrum held in shared memory.
+//
+// The FP32 evaluation order is fixed so that the result is a function of the
+// spectrum bits alone: window maxima are exact; N(w) = (((0 + m_1) + m_2) +
+// ...) / M_valid with every operation rounded on its own; the complement
+// median is an exact order statistic (mean of the two middle values as
+// (a + b) * 0.5f for an even count); SNR = N(w) / B. The best candidate is the
+// largest SNR, the smallest w on ties.
+//
+// The median of the complement of H(w) is found without sorting per
+// candidate. Removing |H(w)| <= h_max = M(2d+1) bins moves the complement's
+// middle ranks by at most h_max in the full order, so one exact selection of
+// the band of full ranks [lo_r, lo_r + bw) around N/2 per pixel suffices:
+// for each candidate, the number of removed bins below the band and the set
+// of removed band positions (a bit mask) locate the complement median inside
+// the band by a find-nth-zero-bit.
+#pragma once
+
+#include "ddhf_internal.cuh"
+
+namespace ddhf {
+
+// Per-warp comb scratch layout (bytes), aliased onto the NDFT staging area.
+struct CombScratch {
+  static constexpr int kBand = 0;                 // bandv[256] f32, bandj[256] i32
+  static constexpr int kHist = 2048;              // hist[2048] u32 (selection)
+  static constexpr int kCand = 2048 + 8192;       // cand[64] u64 (selection)
+  static constexpr int kSelEnd = kCand + 512;
+  static constexpr int kPhase2 = 2048;            // wmax, preb, wmask after selection
+  __host__ __device__ static int bytes(int N, int NW) {
+    int p2 = kPhase2 + 4 * N + ((2 * (N + 1) + 15) & ~15) + 4 * N * NW;
+    return (p2 > kSelEnd ? p2 : kSelEnd);
+  }
+};
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t r;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(r));
+  return r;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_excl_scan(T v, T &total) {
+  const int lane = threadIdx.x & 31;
+  T inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T u = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += u;
+  }
+  total = __shfl_sync(0xffffffffu, inc, 31);
+  return inc - v;
+}
+
+// Bitonic sort (ascending) of S = 2^k u64 keys in shared memory by one warp.
+__device__ __forceinline__ void warp_sort_u64(uint64_t *a, int S) {
+  const int lane = threadIdx.x & 31;
+  for (int k = 2; k <= S; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = lane; i < S; i += 32) {
+        int p = i ^ j;
+        if (p > i) {
+          uint64_t x = a[i], y = a[p];
+          bool up = (i & k) == 0;
+          if ((x > y) == up) {
+            a[i] = y;
+            a[p] = x;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// Composite key of bin j: float bits (P >= 0, so bit order = value order)
+// above the index, giving the (value, index) total order.
+__device__ __forceinline__ uint64_t bin_key(const float *Pw, int j) {
+  return ((uint64_t)__float_as_uint(Pw[j]) << 16) | (uint32_t)j;
+}
+
+// Exact key at full rank R (0-based) by 8-bit radix select over the 48-bit keys.
+__device__ __noinline__ static uint64_t select_rank_slow(const float *Pw, int N, int R, uint32_t *hist) {
+  const int lane = threadIdx.x & 31;
+  uint64_t prefix = 0, pmask = 0;
+  int r = R;
+  for (int shift = 40; shift >= 0; shift -= 8) {
+    for (int i = lane; i < 256; i += 32) hist[i] = 0;
+    __syncwarp();
+    for (int j = lane; j < N; j += 32) {
+      uint64_t key = bin_key(Pw, j);
+      if ((key & pmask) == prefix) atomicAdd(&hist[(key >> shift) & 255], 1u);
+    }
+    __syncwarp();
+    uint32_t h[8], s = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      h[q] = hist[lane * 8 + q];
+      s += h[q];
+    }
+    uint32_t tot;
+    uint32_t ex = warp_excl_scan<uint32_t>(s, tot);
+    bool own = (uint32_t)r >= ex && (uint32_t)r < ex + s;
+    uint32_t ball = __ballot_sync(0xffffffffu, own);
+    int src = __ffs(ball) - 1;
+    int g = 0;
+    uint32_t below = 0;
+    if (lane == src) {
+      uint32_t c = ex;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if ((uint32_t)r >= c && (uint32_t)r < c + h[q]) {
+          g = lane * 8 + q;
+          below = c;
+        }
+        c += h[q];
+      }
+    }
+    g = __shfl_sync(0xffffffffu, g, src);
+    below = __shfl_sync(0xffffffffu, below, src);
+    prefix |= (uint64_t)g << shift;
+    pmask |= (uint64_t)0xFF << shift;
+    r -= (int)below;
+    __syncwarp();
+  }
+  return prefix;
+}
+
+struct CombOut {
+  float log_sf;
+  float snr;
+  int32_t w;
+  uint8_t rotor;
+  uint8_t bad;  // an index check failed (never expected; reported as a device flag)
+};
+
+// Eq. 7-11 for the spectrum Pw[0..N) (shared memory) by the calling warp.
+// scratch: CombScratch::bytes(N, NW) bytes of shared memory (16-byte aligned).
+template <int NW>
+__device__ CombOut comb_warp(const float *Pw, const CombConst &cc, unsigned char *scratch) {
+  const int lane = threadIdx.x & 31;
+  const int N = cc.N;
+  CombOut out;
+  // ---- Eq. 7: spectral flatness, ln SF = mean(ln P) - ln(mean P)
+  float slog = 0.f, sum = 0.f;
+  for (int j = lane; j < N; j += 32) {
+    float v = Pw[j];
+    slog = __fadd_rn(slog, __logf(fmaxf(v, 1e-30f)));
+    sum = __fadd_rn(sum, v);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    slog = __fadd_rn(slog, __shfl_xor_sync(0xffffffffu, slog, o));
+    sum = __fadd_rn(sum, __shfl_xor_sync(0xffffffffu, sum, o));
+  }
+  const float fN = (float)N;
+  out.log_sf = sum > 0.f ? __fsub_rn(__fdiv_rn(slog, fN), __logf(__fdiv_rn(sum, fN))) : 0.f;
+  out.snr = 0.f;
+  out.w = -1;
+  out.rotor = 0;
+  out.bad = 0;
+  if (!(out.log_sf <= cc.ln_tau_sf) || cc.w_hi < cc.w_lo) return out;
+  bool bad = false;
+
+  float *bandv = reinterpret_cast<float *>(scratch + CombScratch::kBand);
+  int32_t *bandj = reinterpret_cast<int32_t *>(scratch + CombScratch::kBand + 1024);
+  uint32_t *hist = reinterpret_cast<uint32_t *>(scratch + CombScratch::kHist);
+  uint64_t *cand = reinterpret_cast<uint64_t *>(scratch + CombScratch::kCand);
+  const int lo_r = cc.lo_r, bw = cc.bw, hi_r = cc.lo_r + cc.bw - 1;
+
+  // ---- band of full ranks [lo_r, hi_r]: 11-bit histogram of the float bits
+  for (int i = lane; i < 2048; i += 32) hist[i] = 0;
+  __syncwarp();
+  for (int j = lane; j < N; j += 32) atomicAdd(&hist[__float_as_uint(Pw[j]) >> 20], 1u);
+  __syncwarp();
+  uint32_t lsum = 0;
+  for (int q = 0; q < 64; ++q) lsum += hist[lane * 64 + ((q + lane) & 63)];  // rotated: no bank conflicts
+  uint32_t tot;
+  uint32_t lex = warp_excl_scan<uint32_t>(lsum, tot);
+  int gsel[2];
+  uint32_t gbelow[2];
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    uint32_t R = t == 0 ? (uint32_t)lo_r : (uint32_t)hi_r;
+    uint32_t ball = __ballot_sync(0xffffffffu, R >= lex && R < lex + lsum);
+    int src = __ffs(ball) - 1;
+    if (src < 0) {
+      src = 0;
+      bad = true;
+    }
+    uint32_t base = __shfl_sync(0xffffffffu, lex, src);
+    uint32_t h0 = hist[src * 64 + 2 * lane], h1 = hist[src * 64 + 2 * lane + 1];
+    uint32_t t2;
+    uint32_t ex2 = warp_excl_scan<uint32_t>(h0 + h1, t2) + base;
+    int g = -1;
+    uint32_t below = 0;
+    if (R >= ex2 && R < ex2 + h0) {
+      g = src * 64 + 2 * lane;
+      below = ex2;
+    } else if (R >= ex2 + h0 && R < ex2 + h0 + h1) {
+      g = src * 64 + 2 * lane + 1;
+      below = ex2 + h0;
+    }
+    uint32_t b2 = __ballot_sync(0xffffffffu, g >= 0);
+    int src2 = __ffs(b2) - 1;
+    if (src2 < 0) {
+      src2 = 0;
+      bad = true;
+    }
+    gsel[t] = __shfl_sync(0xffffffffu, g, src2);
+    gbelow[t] = __shfl_sync(0xffffffffu, below, src2);
+    if (gsel[t] < 0) {
+      gsel[t] = 0;
+      bad = true;
+    }
+  }
+  // candidates: bins whose 11-bit digit lies in [g_lo, g_hi]
+  uint32_t ncand = 0;
+  {
+    uint32_t c_hi_end = 0;
+    // count of elements with digit <= g_hi: gbelow[1] + hist[g_hi]
+    c_hi_end = gbelow[1] + hist[gsel[1]];
+    ncand = c_hi_end - gbelow[0];
+  }
+  __syncwarp();
+  const uint32_t cand_below = gbelow[0];
+  if (ncand <= 64) {
+    uint32_t run = 0;
+    for (int j0 = 0; j0 < N; j0 += 32) {
+      int j = j0 + lane;
+      bool in = false;
+      uint64_t key = 0;
+      if (j < N) {
+        uint32_t u = __float_as_uint(Pw[j]);
+        int g = (int)(u >> 20);
+        in = g >= gsel[0] && g <= gsel[1];
+        key = ((uint64_t)u << 16) | (uint32_t)j;
+      }
+      uint32_t b = __ballot_sync(0xffffffffu, in);
+      if (in) cand[run + __popc(b & lanemask_lt())] = key;
+      run += __popc(b);
+    }
+    for (int i = (int)ncand + lane; i < 64; i += 32) cand[i] = ~0ull;
+    __syncwarp();
+    warp_sort_u64(cand, 64);
+    for (int b = lane; b < bw; b += 32) {
+      int ci = lo_r - (int)cand_below + b;
+      if (ci < 0 || ci >= 64) {
+        ci = ci < 0 ? 0 : 63;
+        bad = true;
+      }
+      uint64_t key = cand[ci];
+      bandv[b] = __uint_as_float((uint32_t)(key >> 16));
+      bandj[b] = (int32_t)(key & 0xFFFF);
+    }
+  } else {
+    uint64_t klo = select_rank_slow(Pw, N, lo_r, hist);
+    uint64_t khi = select_rank_slow(Pw, N, hi_r, hist);
+    uint64_t *buf = reinterpret_cast<uint64_t *>(scratch + CombScratch::kHist);
+    int S = 32;
+    while (S < bw) S <<= 1;
+    uint32_t run = 0;
+    for (int j0 = 0; j0 < N; j0 += 32) {
+      int j = j0 + lane;
+      uint64_t key = j < N ? bin_key(Pw, j) : ~0ull;
+      bool in = j < N && key >= klo && key <= khi;
+      uint32_t b = __ballot_sync(0xffffffffu, in);
+      if (in) buf[run + __popc(b & lanemask_lt())] = key;
+      run += __popc(b);
+    }
+    for (int i = (int)run + lane; i < S; i += 32) buf[i] = ~0ull;
+    __syncwarp();
+    warp_sort_u64(buf, S);
+    for (int b = lane; b < bw; b += 32) {
+      uint64_t key = buf[b];
+      bandv[b] = __uint_as_float((uint32_t)(key >> 16));
+      bandj[b] = (int32_t)(key & 0xFFFF);
+    }
+  }
+  __syncwarp();
+  const uint64_t key_lo = ((uint64_t)__float_as_uint(bandv[0]) << 16) | (uint32_t)bandj[0];
+
+  // ---- phase 2 arrays: window maxima, prefix counts of below-band bins, band masks
+  float *wmax = reinterpret_cast<float *>(scratch + CombScratch::kPhase2);
+  uint16_t *preb = reinterpret_cast<uint16_t *>(scratch + CombScratch::kPhase2 + 4 * N);
+  uint32_t *wmask = reinterpret_cast<uint32_t *>(scratch + CombScratch::kPhase2 + 4 * N +
+                                                 ((2 * (N + 1) + 15) & ~15));
+  const int d = cc.d;
+  for (int c = d + lane; c <= N - 1 - d; c += 32) {
+    float mx = Pw[c - d];
+    for (int i = 1; i <= 2 * d; ++i) mx = fmaxf(mx, Pw[c - d + i]);
+    wmax[c] = mx;
+  }
+  {
+    const int S = (N + 31) / 32;
+    const int j0 = lane * S, j1 = min(N, j0 + S);
+    uint32_t cnt = 0;
+    for (int j = j0; j < j1; ++j) cnt += bin_key(Pw, j) < key_lo ? 1u : 0u;
+    uint32_t total;
+    uint32_t ex = warp_excl_scan<uint32_t>(cnt, total);
+    for (int j = j0; j < j1; ++j) {
+      preb[j] = (uint16_t)ex;
+      ex += bin_key(Pw, j) < key_lo ? 1u : 0u;
+    }
+    if (lane == 31) preb[N] = (uint16_t)total;
+  }
+  for (int i = lane; i < N * NW; i += 32) wmask[i] = 0;
+  __syncwarp();
+  for (int b = lane; b < bw; b += 32) {
+    int jb = bandj[b];
+    for (int c = max(0, jb - d); c <= min(N - 1, jb + d); ++c)
+      atomicOr(&wmask[c * NW + (b >> 5)], 1u << (b & 31));
+  }
+  __syncwarp();
+
+  // ---- Eq. 8-11 over candidate fundamentals
+  float best = 0.f;
+  int bestw = -1;
+  for (int w = cc.w_lo + lane; w <= cc.w_hi; w += 32) {
+    int mv = (N - 1 - d) / w;
+    mv = mv < cc.M ? mv : cc.M;
+    float s = 0.f;
+    uint32_t mask[NW];
+#pragma unroll
+    for (int q = 0; q < NW; ++q) mask[q] = 0;
+    int below = 0, h;
+    for (int m = 1; m <= mv; ++m) {
+      int c = m * w;
+      s = __fadd_rn(s, wmax[c]);
+#pragma unroll
+      for (int q = 0; q < NW; ++q) mask[q] |= wmask[c * NW + q];
+    }
+    if (w >= 2 * d + 1) {
+      h = mv * (2 * d + 1);
+      for (int m = 1; m <= mv; ++m) below += (int)preb[m * w + d + 1] - (int)preb[m * w - d];
+    } else {
+      h = (mv - 1) * w + 2 * d + 1;
+      below = (int)preb[mv * w + d + 1] - (int)preb[w - d];
+    }
+    const int c = N - h;
+    if (c <= 0) continue;
+    const float nw = __fdiv_rn(s, (float)mv);
+    const int base = lo_r - below;
+    const int t1 = (c - 1) / 2 - base, t2 = c / 2 - base;
+    float v[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      int t = k == 0 ? t1 : t2;
+      int pos = -1;
+#pragma unroll
+      for (int q = 0; q < NW; ++q) {
+        if (pos < 0) {
+          uint32_t free_bits = ~mask[q];
+          int nfree = __popc(free_bits);
+          if (t >= 0 && t < nfree) pos = q * 32 + (int)__fns(free_bits, 0, t + 1);
+          else t -= nfree;
+        }
+      }
+      if (pos < 0 || pos >= bw) {
+        pos = 0;
+        bad = true;
+      }
+      v[k] = bandv[pos];
+    }
+    const float B = (c & 1) ? v[0] : __fmul_rn(__fadd_rn(v[0], v[1]), 0.5f);
+    const float snr = B > 0.f ? __fdiv_rn(nw, B) : (nw > 0.f ? __int_as_float(0x7f800000) : 0.f);
+    if (bestw < 0 || snr > best) {
+      best = snr;
+      bestw = w;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    float ob = __shfl_xor_sync(0xffffffffu, best, o);
+    int ow = __shfl_xor_sync(0xffffffffu, bestw, o);
+    bool take = ow >= 0 && (bestw < 0 || ob > best || (ob == best && ow < bestw));
+    if (take) {
+      best = ob;
+      bestw = ow;
+    }
+  }
+  out.bad = __any_sync(0xffffffffu, bad) ? 1 : 0;
+  out.snr = bestw >= 0 ? best : 0.f;
+  out.w = bestw;
+  out.rotor = (bestw >= 0 && best >= cc.tau_comb) ? 1 : 0;
+  __syncwarp();
+  return out;
+}
+
+}  // namespace ddhf

@@ -1,0 +1,180 @@
+// Internal declarations of libddhf: the context, workspace layout, device
+// helpers and the launch functions each translation unit provides.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ddhf.h"
+
+namespace ddhf {
+
+constexpr int kMaxDigitBits = 11;  // at most 2048 bins per radix pass
+constexpr int kBinThreads = 256;   // 8 warps per binning block
+constexpr int kBinItems = 8;       // items per lane per round
+constexpr int kBinRounds = 4;      // rounds per chunk
+constexpr int kBinChunk = kBinThreads * kBinItems * kBinRounds;  // 8192 events
+constexpr int kMaxBandWords = 8;   // comb rank band up to 256 positions
+constexpr uint32_t kSignBit = 0x80000000u;
+
+// Per-window binning output and per-pixel results (one "slot" per window).
+struct Slot {
+  uint32_t *ev = nullptr;       // [max_events] packed events, pixel-major
+  uint32_t *offsets = nullptr;  // [npx + 1]
+  uint32_t *active = nullptr;   // [npx] active pixel keys, ascending
+  uint64_t *counters = nullptr; // [8] n_valid, n_dropped, n_active, n_in, n_heavy, terms, -, n_rotor
+  uint8_t *mask = nullptr;      // [npx] rotor mask
+  int32_t *labels = nullptr;    // [npx]
+  float *log_sf = nullptr;      // [npx] per active pixel (active-list order)
+  float *snr = nullptr;         // [npx]
+  int32_t *f0 = nullptr;        // [npx]
+  int32_t *nbox = nullptr;      // [1]
+  int64_t t0 = 0, window_us = 0;
+};
+
+// Device-visible view of the per-slot arrays for the persistent kernel.
+struct SlotView {
+  const uint32_t *ev;
+  const uint32_t *offsets;
+  const uint32_t *active;
+  const uint64_t *counters;
+  uint8_t *mask;
+  float *log_sf;
+  float *snr;
+  int32_t *f0;
+  int64_t t0;
+};
+
+// Parameters of the comb stage derived once from ddhf_params and the grid.
+struct CombConst {
+  int32_t N;        // bins
+  int32_t M, d, h_min;
+  int32_t w_lo;     // first candidate fundamental: max(1, d)
+  int32_t w_hi;     // last candidate with M_valid >= h_min
+  int32_t lo_r;     // first full rank of the median band
+  int32_t bw;       // band width (positions)
+  float ln_tau_sf;  // log(tau_sf) in FP32
+  float tau_comb;
+};
+
+struct GridConst {
+  uint64_t a0, da, denom;
+  uint64_t barrett;   // floor((2^64 - 1) / denom)
+  uint64_t da_mod;    // da mod denom
+  uint64_t da32_mod;  // 32 da mod denom
+  int32_t N;
+  int32_t nbr;        // b-rows of the blocked form: ceil(N / 32)
+  float two_over_denom;
+};
+
+struct Ctx {
+  int W = 0, H = 0;
+  int64_t npx = 0;
+  ddhf_grid grid{};
+  ddhf_params params{};
+  ddhf_tuning tuning{};
+  int64_t max_events = 0;
+  int max_windows = 0;
+  int device = 0, num_sms = 0;
+  int key_bits = 0, npass = 0;
+  int digit_bits[3] = {0, 0, 0};
+  int64_t nchunks = 0;
+  // sort scratch
+  uint32_t *keysA = nullptr, *valsA = nullptr, *keysB = nullptr, *valsB = nullptr;
+  uint32_t *hist = nullptr;      // [2048 * nchunks]
+  uint32_t *scan_part = nullptr; // block partials of the scans
+  uint32_t *seg_lo = nullptr, *seg_hi = nullptr;  // [npx]
+  uint64_t *packed = nullptr;    // [npx + 1]
+  // per-window slots
+  std::vector<Slot> slots;
+  SlotView *d_views = nullptr;   // [max_windows]
+  // work queue of the persistent kernel
+  uint64_t *work = nullptr;      // [heavy_cap] heavy items (slot << 32 | active index)
+  int64_t heavy_cap = 0;
+  uint32_t *qctl = nullptr;      // [16] queue counters
+  // labelling / boxes scratch
+  int32_t *box_root = nullptr;   // [npx]
+  int32_t *box_tmp = nullptr;    // [npx * 6]
+  uint32_t *flags = nullptr;     // [1] DDHF_FLAG_* bits
+  CombConst comb{};
+  GridConst gconst{};
+  cudaStream_t last_stream = nullptr;
+  bool binned = false;
+  std::string last_error;
+  // stage timing (tracing)
+  bool timing = false;
+  bool timing_recorded = false;
+  cudaEvent_t stage_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  // graph cache of ddhf_detect_batch
+  int64_t graph_kernels = 0;
+  cudaGraphExec_t graph_exec = nullptr;
+  std::vector<uint8_t> graph_key;
+};
+
+// ---------------------------------------------------------------- helpers
+
+#define DDHF_CUDA_TRY(ctx, call)                                                   \
+  do {                                                                             \
+    cudaError_t err__ = (call);                                                    \
+    if (err__ != cudaSuccess) {                                                    \
+      (ctx)->last_error = std::string(#call) + ": " + cudaGetErrorString(err__);   \
+      return DDHF_ERR_CUDA;                                                        \
+    }                                                                              \
+  } while (0)
+
+__host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// (x mod D) for x < 2^64 with a precomputed Barrett factor m = floor(2^64/D).
+__device__ __forceinline__ uint64_t mod_barrett(uint64_t x, uint64_t D, uint64_t m) {
+  uint64_t q = __umul64hi(x, m);
+  uint64_t r = x - q * D;
+  if (r >= D) r -= D;
+  if (r >= D) r -= D;
+  return r;
+}
+
+// e^{-2 pi i r / D} for an exact residue 0 <= r < D, via sincospi on the
+// half-open turn x = 2r/D folded to [-1, 1].
+__device__ __forceinline__ float2 phasor_of_residue(uint64_t r, float two_over_denom) {
+  float x = __fmul_rn((float)r, two_over_denom);
+  if (x > 1.0f) x = __fsub_rn(x, 2.0f);
+  float s, c;
+  sincospif(x, &s, &c);
+  return make_float2(c, -s);
+}
+
+// Complex product with a fixed rounding sequence (no compiler contraction), so
+// every kernel that generates the same phasors gets the same bits.
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(__fmaf_rn(a.x, b.x, -__fmul_rn(a.y, b.y)),
+                     __fmaf_rn(a.x, b.y, __fmul_rn(a.y, b.x)));
+}
+
+// ---------------------------------------------------------- launch entry points
+// bin.cu
+ddhf_status bin_window(Ctx *c, int slot, const int16_t *x, const int16_t *y, const int64_t *t,
+                       const int8_t *p, int64_t n, int64_t t0, int64_t win, cudaStream_t s);
+ddhf_status launch_scan_u32(Ctx *c, const uint32_t *in, uint32_t *out, int64_t n,
+                            cudaStream_t s);
+// ndft.cu
+ddhf_status launch_spectrum(Ctx *c, int form, float *P, int64_t cap_px, cudaStream_t s);
+ddhf_status launch_comb(Ctx *c, const float *P, int64_t cap_px, float *log_sf, float *snr,
+                        int32_t *f0, uint8_t *mask, cudaStream_t s);
+ddhf_status launch_fused(Ctx *c, int n_slots, bool write_p, float *P, int64_t cap_px,
+                         cudaStream_t s);
+void set_bin_attributes();
+// ccl.cu
+ddhf_status launch_label(Ctx *c, const uint8_t *mask, int32_t *labels, uint64_t *n_fg,
+                         cudaStream_t s);
+ddhf_status launch_boxes(Ctx *c, const int32_t *labels, ddhf_box *boxes, int32_t cap,
+                         int32_t *n_boxes, cudaStream_t s);
+
+}  // namespace ddhf
+
+struct ddhf_ctx {
+  ddhf::Ctx c;
+};

@@ -1,0 +1,9 @@
+// Instantiation of the persistent blocked NDFT kernel that writes spectra to
+// global memory (ddhf_power_spectrum with DDHF_FORM_BLOCKED).
+#include "ndft_blocked.cuh"
+
+namespace ddhf {
+ddhf_status launch_blocked_spectrum(Ctx *c, float *P, int64_t cap_px, cudaStream_t s) {
+  return blocked::launch_blocked_any<false>(c, 1, P, cap_px, s);
+}
+}  // namespace ddhf

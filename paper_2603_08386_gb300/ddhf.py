@@ -1,0 +1,356 @@
+"""Python binding of libddhf (include/ddhf.h), argument marshalling only.
+
+Every function named ``ddhf_*`` here calls the C entry point of the same name
+with device pointers taken from torch CUDA tensors and the current torch
+stream; all computation happens in the library's CUDA kernels. A missing or
+unloadable library raises ``DDHFLibraryError``: there is no fallback path.
+
+``Context`` wraps one ``ddhf_ctx`` with tensor-returning helpers.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libddhf.so")
+
+DDHF_OK = 0
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "CAPACITY", 4: "TIMEOUT", 5: "UNSUPPORTED",
+          6: "STATE"}
+FORM = dict(sincos=0, recur=1, blocked=2, naive32=3, kahan=4, f64=5)
+FLAG_CAPACITY, FLAG_TIMEOUT = 1, 2
+
+
+class DDHFLibraryError(RuntimeError):
+    pass
+
+
+class DDHFError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__(f"ddhf status {status} ({STATUS.get(status, '?')}): {msg}")
+
+
+class ddhf_grid(ctypes.Structure):
+    _fields_ = [("a0", ctypes.c_int64), ("da", ctypes.c_int64), ("denom", ctypes.c_int64),
+                ("n_bins", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class ddhf_params(ctypes.Structure):
+    _fields_ = [("tau_sf", ctypes.c_float), ("tau_comb", ctypes.c_float), ("M", ctypes.c_int32),
+                ("d", ctypes.c_int32), ("h_min", ctypes.c_int32), ("n_min", ctypes.c_int32),
+                ("A_min", ctypes.c_int32), ("polarity_01", ctypes.c_int32),
+                ("alpha", ctypes.c_double)]
+
+
+class ddhf_window(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("t_us", ctypes.c_void_p),
+                ("p", ctypes.c_void_p), ("n", ctypes.c_int64), ("t0_us", ctypes.c_int64),
+                ("window_us", ctypes.c_int64)]
+
+
+class ddhf_stats(ctypes.Structure):
+    _fields_ = [("n_in", ctypes.c_int64), ("n_valid", ctypes.c_int64),
+                ("n_dropped", ctypes.c_int64), ("n_active", ctypes.c_int64),
+                ("n_rotor", ctypes.c_int64), ("n_boxes", ctypes.c_int64),
+                ("terms", ctypes.c_int64), ("graph_kernels", ctypes.c_int64),
+                ("device_flags", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+class ddhf_tuning(ctypes.Structure):
+    _fields_ = [("heavy_min", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+# exported symbol -> (restype, argtypes)
+_VP, _I32, _I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+SIGNATURES = {
+    "ddhf_status_string": (ctypes.c_char_p, [_I32]),
+    "ddhf_default_params": (_I32, [ctypes.POINTER(ddhf_params)]),
+    "ddhf_create": (_I32, [_I32, _I32, ctypes.POINTER(ddhf_grid), ctypes.POINTER(ddhf_params),
+                           _I64, _I32, ctypes.POINTER(_VP)]),
+    "ddhf_destroy": (_I32, [_VP]),
+    "ddhf_set_tuning": (_I32, [_VP, ctypes.POINTER(ddhf_tuning)]),
+    "ddhf_get_tuning": (_I32, [_VP, ctypes.POINTER(ddhf_tuning)]),
+    "ddhf_bin_events": (_I32, [_VP, _VP, _VP, _VP, _VP, _I64, _I64, _I64, _VP]),
+    "ddhf_export_csr": (_I32, [_VP, _VP, _VP, _I64, _VP, _VP, _VP]),
+    "ddhf_power_spectrum": (_I32, [_VP, _I32, _VP, _I64, _VP]),
+    "ddhf_comb_score": (_I32, [_VP, _VP, _I64, _VP, _VP, _VP, _VP, _VP]),
+    "ddhf_label": (_I32, [_VP, _VP, _VP, _VP]),
+    "ddhf_boxes": (_I32, [_VP, _VP, _VP, _I32, _VP, _VP]),
+    "ddhf_detect": (_I32, [_VP, _VP, _VP, _VP, _VP, _I64, _I64, _I64, _VP, _I32, _VP, _VP, _VP]),
+    "ddhf_detect_batch": (_I32, [_VP, ctypes.POINTER(ddhf_window), _I32, _VP, _I32, _VP, _VP,
+                                 _I32, _VP]),
+    "ddhf_export_scores": (_I32, [_VP, _I32, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "ddhf_get_stats": (_I32, [_VP, ctypes.POINTER(ddhf_stats)]),
+    "ddhf_enable_stage_timing": (_I32, [_VP, _I32]),
+    "ddhf_stage_times": (_I32, [_VP, ctypes.POINTER(ctypes.c_float)]),
+    "ddhf_last_error": (ctypes.c_char_p, [_VP]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libddhf.so (built by ``build.build()``); raise if it is absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise DDHFLibraryError(f"{path} not found: build it with "
+                                   "paper_2603_08386_gb300.build.build()")
+        try:
+            lib = ctypes.CDLL(path)
+        except OSError as e:
+            raise DDHFLibraryError(f"cannot load {path}: {e}") from e
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream if hasattr(s, "cuda_stream") else int(s)
+
+
+def _check(st, ctx=None):
+    if st != DDHF_OK:
+        msg = ""
+        if ctx:
+            raw = load().ddhf_last_error(ctx)
+            msg = raw.decode() if raw else ""
+        raise DDHFError(st, msg)
+
+
+def make_grid(a0, da, denom, n_bins) -> ddhf_grid:
+    return ddhf_grid(int(a0), int(da), int(denom), int(n_bins), 0)
+
+
+def default_params(**over) -> ddhf_params:
+    p = ddhf_params()
+    _check(load().ddhf_default_params(ctypes.byref(p)))
+    for k, v in over.items():
+        setattr(p, k, v)
+    return p
+
+
+# ---------------------------------------------------------------- same names
+
+def ddhf_create(W, H, grid, params, max_events, max_windows=1):
+    h = ctypes.c_void_p()
+    _check(load().ddhf_create(int(W), int(H), ctypes.byref(grid), ctypes.byref(params),
+                              int(max_events), int(max_windows), ctypes.byref(h)))
+    return h.value
+
+
+def ddhf_destroy(ctx):
+    _check(load().ddhf_destroy(ctx))
+
+
+def ddhf_set_tuning(ctx, heavy_min=1024, warps_per_block=4, blocks_per_sm=0):
+    t = ddhf_tuning(int(heavy_min), int(warps_per_block), int(blocks_per_sm), 0)
+    _check(load().ddhf_set_tuning(ctx, ctypes.byref(t)), ctx)
+
+
+def ddhf_get_tuning(ctx):
+    t = ddhf_tuning()
+    _check(load().ddhf_get_tuning(ctx, ctypes.byref(t)), ctx)
+    return dict(heavy_min=t.heavy_min, warps_per_block=t.warps_per_block,
+                blocks_per_sm=t.blocks_per_sm)
+
+
+def ddhf_bin_events(ctx, x, y, t, p, n, t0, window_us, stream=None):
+    _check(load().ddhf_bin_events(ctx, _ptr(x), _ptr(y), _ptr(t), _ptr(p), int(n), int(t0),
+                                  int(window_us), _stream(stream)), ctx)
+
+
+def ddhf_export_csr(ctx, offsets, ev, cap_ev, active, counts, stream=None):
+    _check(load().ddhf_export_csr(ctx, _ptr(offsets), _ptr(ev), int(cap_ev), _ptr(active),
+                                  _ptr(counts), _stream(stream)), ctx)
+
+
+def ddhf_power_spectrum(ctx, form, P, cap_px, stream=None):
+    _check(load().ddhf_power_spectrum(ctx, int(form), _ptr(P), int(cap_px), _stream(stream)), ctx)
+
+
+def ddhf_comb_score(ctx, P, cap_px, log_sf, snr, f0_bin, mask, stream=None):
+    _check(load().ddhf_comb_score(ctx, _ptr(P), int(cap_px), _ptr(log_sf), _ptr(snr),
+                                  _ptr(f0_bin), _ptr(mask), _stream(stream)), ctx)
+
+
+def ddhf_label(ctx, mask, labels, stream=None):
+    _check(load().ddhf_label(ctx, _ptr(mask), _ptr(labels), _stream(stream)), ctx)
+
+
+def ddhf_boxes(ctx, labels, boxes, cap, n_boxes, stream=None):
+    _check(load().ddhf_boxes(ctx, _ptr(labels), _ptr(boxes), int(cap), _ptr(n_boxes),
+                             _stream(stream)), ctx)
+
+
+def ddhf_detect(ctx, x, y, t, p, n, t0, window_us, boxes, cap, n_boxes, mask_out=None,
+                stream=None):
+    _check(load().ddhf_detect(ctx, _ptr(x), _ptr(y), _ptr(t), _ptr(p), int(n), int(t0),
+                              int(window_us), _ptr(boxes), int(cap), _ptr(n_boxes),
+                              _ptr(mask_out), _stream(stream)), ctx)
+
+
+def ddhf_detect_batch(ctx, windows, boxes, cap, n_boxes, masks_out=None, use_graph=False,
+                      stream=None):
+    """windows: list of (x, y, t, p, n, t0, window_us) with device tensors."""
+    arr = (ddhf_window * len(windows))()
+    for i, (x, y, t, p, n, t0, win) in enumerate(windows):
+        arr[i] = ddhf_window(_ptr(x), _ptr(y), _ptr(t), _ptr(p), int(n), int(t0), int(win))
+    _check(load().ddhf_detect_batch(ctx, arr, len(windows), _ptr(boxes), int(cap), _ptr(n_boxes),
+                                    _ptr(masks_out), int(bool(use_graph)), _stream(stream)), ctx)
+
+
+def ddhf_export_scores(ctx, slot, active, log_sf, snr, f0_bin, counts, stream=None):
+    _check(load().ddhf_export_scores(ctx, int(slot), _ptr(active), _ptr(log_sf), _ptr(snr),
+                                     _ptr(f0_bin), _ptr(counts), _stream(stream)), ctx)
+
+
+def ddhf_enable_stage_timing(ctx, enable=True):
+    _check(load().ddhf_enable_stage_timing(ctx, int(bool(enable))), ctx)
+
+
+def ddhf_stage_times(ctx):
+    """Device milliseconds of {binning, fused classify, labels + boxes} of the
+    last timed detection call."""
+    out = (ctypes.c_float * 3)()
+    _check(load().ddhf_stage_times(ctx, out), ctx)
+    return [float(v) for v in out]
+
+
+def ddhf_get_stats(ctx, raise_on_flags=True):
+    s = ddhf_stats()
+    st = load().ddhf_get_stats(ctx, ctypes.byref(s))
+    out = {k: getattr(s, k) for k, _ in ddhf_stats._fields_ if k != "reserved"}
+    out["status"] = st
+    if raise_on_flags:
+        _check(st, ctx)
+    return out
+
+
+# ---------------------------------------------------------------- convenience
+
+class Context:
+    """One ddhf context bound to the current CUDA device."""
+
+    def __init__(self, W, H, grid, params=None, max_events=1 << 20, max_windows=1):
+        if isinstance(grid, tuple):
+            grid = make_grid(*grid)
+        self.W, self.H, self.npx = int(W), int(H), int(W) * int(H)
+        self.grid = grid
+        self.n_bins = grid.n_bins
+        self.params = params if params is not None else default_params()
+        self.max_events = int(max_events)
+        self.max_windows = int(max_windows)
+        self.dev = torch.device("cuda", torch.cuda.current_device())
+        self.h = ddhf_create(W, H, grid, self.params, max_events, max_windows)
+
+    def close(self):
+        if self.h:
+            ddhf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_tuning(self, **kw):
+        cur = ddhf_get_tuning(self.h)
+        cur.update(kw)
+        ddhf_set_tuning(self.h, **cur)
+
+    def bin_events(self, x, y, t, p, t0, window_us):
+        ddhf_bin_events(self.h, x, y, t, p, x.numel(), t0, window_us)
+
+    def csr(self, cap_ev=None):
+        cap_ev = self.max_events if cap_ev is None else cap_ev
+        off = torch.empty(self.npx + 1, dtype=torch.int32, device=self.dev)
+        ev = torch.empty(max(cap_ev, 1), dtype=torch.int32, device=self.dev)
+        act = torch.empty(self.npx, dtype=torch.int32, device=self.dev)
+        cnt = torch.zeros(4, dtype=torch.int64, device=self.dev)
+        ddhf_export_csr(self.h, off, ev, cap_ev, act, cnt)
+        c = cnt.cpu().tolist()
+        return dict(offsets=off, ev=ev[: c[0]], active=act[: c[2]], n_valid=c[0],
+                    n_dropped=c[1], n_active=c[2], n_in=c[3])
+
+    def n_active(self):
+        cnt = torch.zeros(4, dtype=torch.int64, device=self.dev)
+        ddhf_export_csr(self.h, None, None, 0, None, cnt)
+        return int(cnt[2].item())
+
+    def power_spectrum(self, form="blocked", cap_px=None):
+        f = FORM[form] if isinstance(form, str) else int(form)
+        na = self.n_active() if cap_px is None else cap_px
+        P = torch.empty((max(na, 1), self.n_bins), dtype=torch.float32, device=self.dev)
+        ddhf_power_spectrum(self.h, f, P, na)
+        return P[:na]
+
+    def comb_score(self, P):
+        na = P.shape[0]
+        lsf = torch.empty(max(na, 1), dtype=torch.float32, device=self.dev)
+        snr = torch.empty_like(lsf)
+        f0 = torch.empty(max(na, 1), dtype=torch.int32, device=self.dev)
+        mask = torch.empty(self.npx, dtype=torch.uint8, device=self.dev)
+        ddhf_comb_score(self.h, P.contiguous() if na else lsf, na, lsf, snr, f0, mask)
+        return dict(log_sf=lsf[:na], snr=snr[:na], f0_bin=f0[:na], mask=mask)
+
+    def label(self, mask):
+        lab = torch.empty(self.npx, dtype=torch.int32, device=self.dev)
+        ddhf_label(self.h, mask.contiguous(), lab)
+        return lab
+
+    def boxes(self, labels, cap=4096):
+        bx = torch.empty((max(cap, 1), 5), dtype=torch.int32, device=self.dev)
+        nb = torch.zeros(1, dtype=torch.int32, device=self.dev)
+        ddhf_boxes(self.h, labels, bx, cap, nb)
+        n = int(nb.item())
+        return bx[: min(n, cap)], n
+
+    def detect(self, x, y, t, p, t0, window_us, cap=4096, want_mask=False):
+        bx = torch.empty((max(cap, 1), 5), dtype=torch.int32, device=self.dev)
+        nb = torch.zeros(1, dtype=torch.int32, device=self.dev)
+        mask = torch.empty(self.npx, dtype=torch.uint8, device=self.dev) if want_mask else None
+        ddhf_detect(self.h, x, y, t, p, x.numel(), t0, window_us, bx, cap, nb, mask)
+        return bx, nb, mask
+
+    def scores(self, slot=0):
+        act = torch.empty(self.npx, dtype=torch.int32, device=self.dev)
+        lsf = torch.empty(self.npx, dtype=torch.float32, device=self.dev)
+        snr = torch.empty_like(lsf)
+        f0 = torch.empty(self.npx, dtype=torch.int32, device=self.dev)
+        cnt = torch.zeros(4, dtype=torch.int64, device=self.dev)
+        ddhf_export_scores(self.h, slot, act, lsf, snr, f0, cnt)
+        na = int(cnt[2].item())
+        return dict(active=act[:na], log_sf=lsf[:na], snr=snr[:na], f0_bin=f0[:na], n_active=na)
+
+    def stats(self, raise_on_flags=True):
+        return ddhf_get_stats(self.h, raise_on_flags)
+
+
+def events_to_device(scene, device="cuda"):
+    """Upload a synthetic Scene's event arrays to device tensors."""
+    return (torch.from_numpy(scene.x).to(device), torch.from_numpy(scene.y).to(device),
+            torch.from_numpy(scene.t).to(device), torch.from_numpy(scene.p).to(device))

@@ -343,3 +343,29 @@ def small_scene(seed: int, W: int = 48, H: int = 40, window_us: int = 20_000,
         s.t = np.insert(s.t, at, bt + s.t0)
         s.p = np.insert(s.p, at, bp)
     return s
+
+
+def synthetic_spectra(n_px: int, N: int, seed: int) -> np.ndarray:
+    """Seeded FP32 power spectra [n_px, N] for scoring tests: exponential noise
+    rows, rows with harmonic combs (one or two fundamentals, peaks spread over
+    +-1 bin), rows with repeated values, zero bins and constant rows."""
+    rng = np.random.default_rng(seed)
+    P = rng.exponential(1.0, (n_px, N)).astype(np.float32)
+    kind = rng.integers(0, 6, n_px)
+    for i in range(n_px):
+        k = kind[i]
+        if k in (1, 2):
+            for _ in range(k):
+                w = int(rng.integers(3, max(4, N // 5)))
+                amp = float(rng.uniform(2.0, 40.0))
+                for m in range(1, 7):
+                    c = m * w + int(rng.integers(-1, 2))
+                    if 0 <= c < N:
+                        P[i, c] += np.float32(amp * rng.uniform(0.5, 1.0))
+        elif k == 3:
+            P[i] = np.round(P[i] * 4.0) / 4.0  # many exact ties
+        elif k == 4:
+            P[i, rng.random(N) < 0.3] = 0.0
+        elif k == 5 and rng.random() < 0.3:
+            P[i] = np.float32(rng.uniform(0.5, 2.0))  # constant row
+    return P
