@@ -50,9 +50,9 @@ def _gen_window(args):
     return sc.x, sc.y, sc.t, sc.p, sc.t0, sc.window_us, sc.n
 
 
-def generate(rank: int, procs: int):
+def generate(rank: int, procs: int, n_windows: int = N_STREAMS * N_WINDOWS):
     seed = 1003 + 1000 * rank
-    jobs = [(seed, s, w) for s in range(N_STREAMS) for w in range(N_WINDOWS)]
+    jobs = [(seed, s, w) for s in range(N_STREAMS) for w in range(N_WINDOWS)][:n_windows]
     ctx = mp.get_context("spawn")
     with ctx.Pool(processes=max(1, min(procs, len(jobs)))) as pool:
         return pool.map(_gen_window, jobs, chunksize=1)
@@ -120,12 +120,17 @@ class Clocks:
                     samples=len(rows), power_w_max=max(power) if power else None)
 
 
-def oracle_sample(win, W, H, grid, n_pixels, seed=5):
-    """FP64 oracle (as it stands) on a seeded sample of one window's active pixels:
-    per-pixel NDFT + SF + comb (Eq. 6-11). Returns (terms, seconds, pixels)."""
+def oracle_bin(win, W, H):
     import oracle
     x, y, t, p, t0, wus, n = win
-    b = oracle.bin_events(W, H, x, y, t, p, t0, wus)
+    return oracle.bin_events(W, H, x, y, t, p, t0, wus)
+
+
+def oracle_sample(b, W, H, grid, n_pixels, seed=5):
+    """FP64 oracle (as it stands) on a seeded sample of one binned window's
+    active pixels: per-pixel NDFT + SF + comb (Eq. 6-11).
+    Returns (terms, seconds, pixels)."""
+    import oracle
     act = np.flatnonzero(b["counts"] >= 6)
     rng = np.random.default_rng(seed)
     pix = np.sort(rng.choice(act, size=min(n_pixels, act.size), replace=False))
@@ -141,13 +146,13 @@ def run_reference(args):
     if rank != 0:
         return
     sc = synth.config3_window(0, 0)
-    win = (sc.x, sc.y, sc.t, sc.p, sc.t0, sc.window_us, sc.n)
+    b = oracle_bin((sc.x, sc.y, sc.t, sc.p, sc.t0, sc.window_us, sc.n), sc.W, sc.H)
     per_step = 60
     for i in range(args.warmup):
-        oracle_sample(win, sc.W, sc.H, sc.grid, 8, seed=100 + i)
+        oracle_sample(b, sc.W, sc.H, sc.grid, 8, seed=100 + i)
     tot_terms, tot_s = 0, 0.0
     for i in range(args.steps):
-        tr, s, _ = oracle_sample(win, sc.W, sc.H, sc.grid, per_step, seed=1000 + i)
+        tr, s, _ = oracle_sample(b, sc.W, sc.H, sc.grid, per_step, seed=1000 + i)
         tot_terms += tr
         tot_s += s
     v = tot_terms / tot_s
@@ -172,6 +177,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-pipeline comparison")
     ap.add_argument("--no-oracle", action="store_true", help="skip the CPU baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer e2e loop")
+    ap.add_argument("--windows", type=int, default=N_STREAMS * N_WINDOWS,
+                    help="windows per step (default 32; fewer only for profiling cases)")
     ap.add_argument("--procs", type=int, default=int(os.environ.get("DDHF_GEN_PROCS", "16")))
     args = ap.parse_args()
     if args.impl == "reference":
@@ -181,7 +189,7 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     # inputs are generated before any CUDA call (spawned workers)
-    wins = generate(rank, max(1, args.procs // max(1, world)))
+    wins = generate(rank, max(1, args.procs // max(1, world)), args.windows)
 
     import torch
     from paper_2603_08386_gb300 import build, ddhf
@@ -244,36 +252,39 @@ def main():
     value = terms_step * world * args.steps / (ms * 1e-3)
     st = ctx.stats()
     # ------------------------------------------------------------ e2e from pinned host memory
-    host = [tuple(torch.from_numpy(a).pin_memory() for a in w[:4]) for w in wins]
-    h2d = sum(sum(a.numel() * a.element_size() for a in hw) for hw in host)
-    hbox = torch.empty((nwin * cap, 5), dtype=torch.int32).pin_memory()
-    hn = torch.empty(nwin, dtype=torch.int32).pin_memory()
-    d2h = hbox.numel() * 4 + hn.numel() * 4
+    e2e = None
+    if not args.no_e2e:
+        host = [tuple(torch.from_numpy(a).pin_memory() for a in w[:4]) for w in wins]
+        h2d = sum(sum(a.numel() * a.element_size() for a in hw) for hw in host)
+        hbox = torch.empty((nwin * cap, 5), dtype=torch.int32).pin_memory()
+        hn = torch.empty(nwin, dtype=torch.int32).pin_memory()
+        d2h = hbox.numel() * 4 + hn.numel() * 4
 
-    def e2e_step():
-        for d, hw in zip(dev, host):
-            for dst, src in zip(d, hw):
-                dst.copy_(src, non_blocking=True)
-        step()
-        hbox.copy_(boxes, non_blocking=True)
-        hn.copy_(nbox, non_blocking=True)
+        def e2e_step():
+            for d, hw in zip(dev, host):
+                for dst, src in zip(d, hw):
+                    dst.copy_(src, non_blocking=True)
+            step()
+            hbox.copy_(boxes, non_blocking=True)
+            hn.copy_(nbox, non_blocking=True)
 
-    e2e_step()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    e2e_steps = max(1, min(args.steps, 5))
-    e0.record()
-    for _ in range(e2e_steps):
         e2e_step()
-    e1.record()
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    if dist:
-        tt = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
-    e2e_value = terms_step * world * e2e_steps / (e2e_ms * 1e-3)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        e2e_steps = max(1, min(args.steps, 5))
+        e0.record()
+        for _ in range(e2e_steps):
+            e2e_step()
+        e1.record()
+        torch.cuda.synchronize()
+        e2e_ms = e0.elapsed_time(e1)
+        if dist:
+            tt = torch.tensor([e2e_ms], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_ms = float(tt.item())
+        e2e = dict(value=terms_step * world * e2e_steps / (e2e_ms * 1e-3), unit=UNIT,
+                   h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h, steps=e2e_steps)
     # ------------------------------------------------------------ plain per-pixel pipeline
     plain = None
     if not args.no_plain:
@@ -312,7 +323,7 @@ def main():
     # ------------------------------------------------------------ CPU baseline (oracle)
     cpu = None
     if rank == 0 and world == 1 and not args.no_oracle:
-        tr, secs, npix = oracle_sample(wins[0], W, H, grid, 1200)
+        tr, secs, npix = oracle_sample(oracle_bin(wins[0], W, H), W, H, grid, 1200)
         cpu = dict(value=tr / secs, unit=UNIT, cores=1, kind="oracle",
                    sample=f"{npix} seeded random active pixels of window 0 of stream 0: "
                           f"FP64 NDFT + SF + comb (Eq. 6-11), {secs:.1f} s single-threaded")
@@ -337,8 +348,7 @@ def main():
                       kernel="fused blocked NDFT + SF + comb (k_blocked<6,1,true>)",
                       ops="3 FP32 FMA-pipe lane-ops per term (three-multiplication complex "
                           "product); peak = 152 SMs x 128 FP32 lanes x 2070 MHz"),
-        e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
-                 steps=e2e_steps),
+        e2e=e2e,
         gpu_launches=int(graph_kernels) * args.steps,
         clocks=clk,
         plain=plain,

@@ -172,18 +172,29 @@ ddhf_status bin_into(Ctx *c, int slot, const int16_t *x, const int16_t *y, const
   return bin_window(c, slot, x, y, t, p, n, t0, win, s);
 }
 
+// Stage event: an external event node while the stream is being captured into
+// a graph, a plain record otherwise.
+cudaError_t record_stage(Ctx *c, int i, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(s, &cs);
+  if (e != cudaSuccess) return e;
+  if (cs == cudaStreamCaptureStatusActive)
+    return cudaEventRecordWithFlags(c->stage_ev[i], s, cudaEventRecordExternal);
+  return cudaEventRecord(c->stage_ev[i], s);
+}
+
 ddhf_status run_detect(Ctx *c, const ddhf_window *wins, int nw, ddhf_box *boxes, int32_t cap,
                        int32_t *n_boxes_dev, uint8_t *masks_out, cudaStream_t s) {
-  if (c->timing) DDHF_CUDA_TRY(c, cudaEventRecord(c->stage_ev[0], s));
+  if (c->timing) DDHF_CUDA_TRY(c, record_stage(c, 0, s));
   DDHF_CUDA_TRY(c, cudaMemsetAsync(c->qctl, 0, sizeof(uint32_t), s));  // heavy count
   for (int w = 0; w < nw; ++w) {
     const ddhf_window &W = wins[w];
     DDHF_CUDA_TRY(c, cudaMemsetAsync(c->slots[w].mask, 0, c->npx, s));
     DDHF_TRY(bin_into(c, w, W.x, W.y, W.t_us, W.p, W.n, W.t0_us, W.window_us, s));
   }
-  if (c->timing) DDHF_CUDA_TRY(c, cudaEventRecord(c->stage_ev[1], s));
+  if (c->timing) DDHF_CUDA_TRY(c, record_stage(c, 1, s));
   DDHF_TRY(launch_fused(c, nw, true, nullptr, 0, s));
-  if (c->timing) DDHF_CUDA_TRY(c, cudaEventRecord(c->stage_ev[2], s));
+  if (c->timing) DDHF_CUDA_TRY(c, record_stage(c, 2, s));
   for (int w = 0; w < nw; ++w) {
     Slot &sl = c->slots[w];
     DDHF_TRY(launch_label(c, sl.mask, sl.labels, sl.counters + 7, s));
@@ -195,7 +206,7 @@ ddhf_status run_detect(Ctx *c, const ddhf_window *wins, int nw, ddhf_box *boxes,
                                        cudaMemcpyDeviceToDevice, s));
   }
   if (c->timing) {
-    DDHF_CUDA_TRY(c, cudaEventRecord(c->stage_ev[3], s));
+    DDHF_CUDA_TRY(c, record_stage(c, 3, s));
     c->timing_recorded = true;
   }
   return DDHF_OK;

@@ -116,16 +116,26 @@ __global__ void k_box_root_init(const int32_t *__restrict__ lab, int32_t *bx, in
   }
 }
 
+// Pixels of one component usually share a warp, so the bounds are first
+// reduced among the lanes with the same root and one lane updates the slot.
 __global__ void k_box_accum(const int32_t *__restrict__ lab, int32_t *bx, int W, int64_t npx) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npx;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int r = lab[i];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < npx; base += stride) {
+    const int64_t i = base + threadIdx.x;
+    const int r = i < npx ? lab[i] : -1;
+    const uint32_t peers = __match_any_sync(0xffffffffu, r);
     if (r < 0) continue;
     const int x = (int)(i % W), y = (int)(i / W);
-    atomicMin(&bx[r], x);
-    atomicMax(&bx[2 * npx + r], x);
-    atomicMax(&bx[3 * npx + r], y);
-    atomicAdd(&bx[4 * npx + r], 1);
+    const int xmin = __reduce_min_sync(peers, x);
+    const int xmax = __reduce_max_sync(peers, x);
+    const int ymax = __reduce_max_sync(peers, y);
+    const int n = __popc(peers);
+    if ((threadIdx.x & 31) == __ffs(peers) - 1) {
+      atomicMin(&bx[r], xmin);
+      atomicMax(&bx[2 * npx + r], xmax);
+      atomicMax(&bx[3 * npx + r], ymax);
+      atomicAdd(&bx[4 * npx + r], n);
+    }
   }
 }
 

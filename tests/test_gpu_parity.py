@@ -337,16 +337,20 @@ def test_batch_graph_equals_single_windows():
     boxes = torch.empty((len(scenes) * cap, 5), dtype=torch.int32, device="cuda")
     nbx = torch.zeros(len(scenes), dtype=torch.int32, device="cuda")
     masks = torch.empty((len(scenes), W * H), dtype=torch.uint8, device="cuda")
+    ddhf.ddhf_enable_stage_timing(cb.h, True)
     for use_graph in (False, True, True):
         boxes.fill_(-7)
         masks.fill_(3)
         ddhf.ddhf_detect_batch(cb.h, wins, boxes, cap, nbx, masks, use_graph=use_graph)
+        times = ddhf.ddhf_stage_times(cb.h)
+        assert all(t > 0 for t in times)
         torch.cuda.synchronize()
         for i, (bref, mref) in enumerate(single):
             n = int(nbx[i].item())
             assert torch.equal(boxes[i * cap: i * cap + n], bref)
             assert torch.equal(masks[i], mref)
-    cb.stats()
+    st = cb.stats()
+    assert st["graph_kernels"] > 3 * len(scenes)
     cb.close()
 
 
