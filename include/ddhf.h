@@ -260,6 +260,29 @@ ddhf_status ddhf_export_scores(ddhf_ctx *ctx, int32_t slot, uint32_t *active, fl
 ddhf_status ddhf_enable_stage_timing(ddhf_ctx *ctx, int32_t enable);
 ddhf_status ddhf_stage_times(ddhf_ctx *ctx, float *out_ms);
 
+/* Spectra without any device allocation. The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory while
+ * running (for example an embedded real-time detector whose memory is all
+ * reserved at start-up, since cudaMalloc may synchronise the device for
+ * milliseconds, or a host program whose own allocator owns the device), and
+ * so cannot create a context.
+ * Computes the same P as ddhf_power_spectrum(DDHF_FORM_BLOCKED) with the
+ * default tuning, from a per-pixel list the caller built and owns (device
+ * pointers, the layout ddhf_export_csr writes): offsets[k] .. offsets[k+1]
+ * index ev (packed tau | sign << 31) for pixel key k; active[n_active] lists
+ * the pixel keys to evaluate; P[a * n_bins + j] for a < n_active (cap_px >=
+ * n_active required). grid is a host pointer.
+ * Limits: n_events <= 2^25 events in ev, n_active <= 2^26. Larger sizes
+ * return DDHF_ERR_INVALID_ARG. Its scratch is one fixed 256 KiB __device__
+ * array (kept by every device that loads the library until exit); the first
+ * call on a device looks up that array's address, so make it before any
+ * stream capture. All calls share the array, so calls that overlap on the
+ * GPU race: serialise them. */
+ddhf_status ddhf_power_spectrum_noalloc(const ddhf_grid *grid, const uint32_t *offsets,
+                                        const uint32_t *ev, int64_t n_events,
+                                        const uint32_t *active, int64_t n_active, float *P,
+                                        int64_t cap_px, ddhf_stream stream);
+
 /* Synchronise the context's last stream and read its counters and device
  * flags. Returns DDHF_ERR_CAPACITY / DDHF_ERR_TIMEOUT when the matching
  * flag is set (the stats are filled either way); the flags are then cleared. */

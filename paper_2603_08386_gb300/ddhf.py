@@ -90,6 +90,8 @@ SIGNATURES = {
     "ddhf_enable_stage_timing": (_I32, [_VP, _I32]),
     "ddhf_stage_times": (_I32, [_VP, ctypes.POINTER(ctypes.c_float)]),
     "ddhf_last_error": (ctypes.c_char_p, [_VP]),
+    "ddhf_power_spectrum_noalloc": (_I32, [ctypes.POINTER(ddhf_grid), _VP, _VP, _I64, _VP, _I64,
+                                           _VP, _I64, _VP]),
 }
 
 _lib = None
@@ -237,6 +239,15 @@ def ddhf_stage_times(ctx):
     out = (ctypes.c_float * 3)()
     _check(load().ddhf_stage_times(ctx, out), ctx)
     return [float(v) for v in out]
+
+
+def ddhf_power_spectrum_noalloc(grid, offsets, ev, n_events, active, n_active, P, cap_px,
+                                stream=None):
+    """Blocked-form spectra from a caller-owned per-pixel list; the library
+    allocates nothing (see include/ddhf.h for who needs this and its limits)."""
+    _check(load().ddhf_power_spectrum_noalloc(ctypes.byref(grid), _ptr(offsets), _ptr(ev),
+                                              int(n_events), _ptr(active), int(n_active),
+                                              _ptr(P), int(cap_px), _stream(stream)))
 
 
 def ddhf_get_stats(ctx, raise_on_flags=True):
