@@ -23,19 +23,22 @@ namespace ddhf {
 
 // Per-warp comb scratch layout (bytes), aliased onto the NDFT staging area.
 //   [0, 2048)       band values (f32[256]) and band indices (i32[256])
-//   [2048, 6144)    selection histogram (u32[1024]); later window maxima f32[N]
+//   [2048, 6144)    selection histogram (u32[1024])
 //   [6144, 6656)    selection candidates (u64[64])
-//   after wmax      below-band ballot words and their prefix counts (u32 each)
+//   from 2048, after the selection: window maxima f32[N], below-band prefix
+//   counts u16[N+1], band masks per window centre u32[N][NW]
 struct CombScratch {
   static constexpr int kBand = 0;
   static constexpr int kHist = 2048;
   static constexpr int kCand = 6144;
   static constexpr int kSelEnd = 6656;
   static constexpr int kPhase2 = 2048;
-  // ballot words cover bins 0..N inclusive (a count "below bin N" is a query)
-  __host__ __device__ static int words(int N) { return N / 32 + 1; }
-  __host__ __device__ static int bytes(int N, int) {
-    int p2 = kPhase2 + 4 * N + 8 * words(N);
+  __host__ __device__ static int preb_off(int N) { return kPhase2 + 4 * N; }
+  __host__ __device__ static int wmask_off(int N) {
+    return preb_off(N) + ((2 * (N + 1) + 15) & ~15);
+  }
+  __host__ __device__ static int bytes(int N, int NW) {
+    int p2 = wmask_off(N) + 4 * N * NW;
     p2 = (p2 + 15) & ~15;
     return p2 > kSelEnd ? p2 : kSelEnd;
   }
@@ -144,29 +147,27 @@ struct CombOut {
 
 // Bitonic sort (ascending) of 64 u64 keys held two per lane (element i = lane
 // + 32 s in register v[s]) by warp shuffles.
-__device__ __forceinline__ void warp_sort64_regs(uint64_t (&v)[2]) {
+__device__ __forceinline__ void warp_sort64_regs(uint64_t &v0, uint64_t &v1) {
   const int lane = threadIdx.x & 31;
-#pragma unroll
+#pragma unroll 1
   for (int k = 2; k <= 64; k <<= 1) {
-#pragma unroll
+#pragma unroll 1
     for (int j = k >> 1; j > 0; j >>= 1) {
       if (j == 32) {
-        if (v[0] > v[1]) {  // k = 64: the whole sequence ascends
-          uint64_t t = v[0];
-          v[0] = v[1];
-          v[1] = t;
+        if (v0 > v1) {  // k = 64: the whole sequence ascends
+          const uint64_t t = v0;
+          v0 = v1;
+          v1 = t;
         }
       } else {
-#pragma unroll
-        for (int sidx = 0; sidx < 2; ++sidx) {
-          const int i = lane + 32 * sidx;
-          const uint64_t o = __shfl_xor_sync(0xffffffffu, v[sidx], j);
-          const bool up = (i & k) == 0;
-          const bool lower = (i & j) == 0;
-          const uint64_t mn = v[sidx] < o ? v[sidx] : o;
-          const uint64_t mx = v[sidx] < o ? o : v[sidx];
-          v[sidx] = (lower == up) ? mn : mx;
-        }
+        const bool lower = (lane & j) == 0;
+        const uint64_t o0 = __shfl_xor_sync(0xffffffffu, v0, j);
+        const uint64_t o1 = __shfl_xor_sync(0xffffffffu, v1, j);
+        const bool up0 = (lane & k) == 0, up1 = ((lane + 32) & k) == 0;
+        const uint64_t mn0 = v0 < o0 ? v0 : o0, mx0 = v0 < o0 ? o0 : v0;
+        const uint64_t mn1 = v1 < o1 ? v1 : o1, mx1 = v1 < o1 ? o1 : v1;
+        v0 = (lower == up0) ? mn0 : mx0;
+        v1 = (lower == up1) ? mn1 : mx1;
       }
     }
   }
@@ -177,20 +178,6 @@ __device__ __forceinline__ int lin_bucket(float v, float scale) {
   return (int)fminf(__fmul_rn(v, scale), 1023.f);
 }
 
-// Number of bins j' < j below the band (from the ballot words and their prefix).
-__device__ __forceinline__ int below_before(const uint32_t *bwords, const uint32_t *bbase, int j) {
-  const int w = j >> 5, b = j & 31;
-  return (int)bbase[w] + __popc(bwords[w] & ((1u << b) - 1u));
-}
-
-// Eq. 8 numerator sum and its division by M_valid, in the fixed FP32 order.
-__device__ __forceinline__ float comb_nw(const float *wmax, int w, int mv) {
-  float s = 0.f;
-  for (int m = 1; m <= mv; ++m) s = __fadd_rn(s, wmax[m * w]);
-  if ((mv & (mv - 1)) == 0) return __fmul_rn(s, 1.0f / (float)mv);  // exact: power of two
-  return __fdiv_rn(s, (float)mv);
-}
-
 __device__ __forceinline__ float snr_of(float nw, float B) {
   return B > 0.f ? __fdiv_rn(nw, B) : (nw > 0.f ? __int_as_float(0x7f800000) : 0.f);
 }
@@ -198,7 +185,8 @@ __device__ __forceinline__ float snr_of(float nw, float B) {
 // Eq. 7-11 for the spectrum Pw[0..N) (shared memory) by the calling warp.
 // scratch: CombScratch::bytes(N, NW) bytes of shared memory (16-byte aligned).
 template <int NW>
-__device__ CombOut comb_warp(const float *Pw, const CombConst &cc, unsigned char *scratch) {
+__device__ __forceinline__ CombOut comb_warp(const float *Pw, const CombConst &cc,
+                                             unsigned char *scratch) {
   const int lane = threadIdx.x & 31;
   const int N = cc.N;
   CombOut out;
@@ -233,13 +221,13 @@ __device__ CombOut comb_warp(const float *Pw, const CombConst &cc, unsigned char
   // 1024 linear buckets over [0, 2 * mean): the band usually falls into a few
   // buckets holding ~bw + 2 values, which are then sorted exactly.
   const float scale = __fdiv_rn(512.f, __fdiv_rn(sum, fN));
-#pragma unroll
+#pragma unroll 4
   for (int q = 0; q < 32; ++q) hist[q * 32 + lane] = 0;
   __syncwarp();
   for (int j = lane; j < N; j += 32) atomicAdd(&hist[lin_bucket(Pw[j], scale)], 1u);
   __syncwarp();
   uint32_t lsum = 0;
-#pragma unroll 8
+#pragma unroll 4
   for (int q = 0; q < 32; ++q) lsum += hist[lane * 32 + ((q + lane) & 31)];  // rotated: no conflicts
   uint32_t tot;
   const uint32_t lex = warp_excl_scan<uint32_t>(lsum, tot);
@@ -290,7 +278,7 @@ __device__ CombOut comb_warp(const float *Pw, const CombConst &cc, unsigned char
     uint64_t v2[2];
     v2[0] = lane < (int)ncand ? cand[lane] : ~0ull;
     v2[1] = lane + 32 < (int)ncand ? cand[lane + 32] : ~0ull;
-    warp_sort64_regs(v2);
+    warp_sort64_regs(v2[0], v2[1]);
     // sorted element i sits in lane i % 32, register i / 32
     for (int b0 = 0; b0 < bw; b0 += 32) {
       const int i = lo_r - (int)cand_below + b0 + lane;
@@ -329,127 +317,107 @@ __device__ CombOut comb_warp(const float *Pw, const CombConst &cc, unsigned char
     }
   }
   __syncwarp();
-  const float v_lo = bandv[0], v_hi = bandv[bw - 1];
-  const uint64_t key_lo = ((uint64_t)__float_as_uint(v_lo) << 16) | (uint32_t)bandj[0];
+  const uint64_t key_lo = ((uint64_t)__float_as_uint(bandv[0]) << 16) | (uint32_t)bandj[0];
 
-  // ---- window maxima, below-band ballot words
+  // ---- per-bin prefix of below-band counts, window maxima, per-centre band masks
   const int d = cc.d;
   float *wmax = reinterpret_cast<float *>(scratch + CombScratch::kPhase2);
-  uint32_t *bwords = reinterpret_cast<uint32_t *>(scratch + CombScratch::kPhase2 + 4 * N);
-  uint32_t *bbase = bwords + CombScratch::words(N);
+  uint16_t *preb = reinterpret_cast<uint16_t *>(scratch + CombScratch::preb_off(N));
+  uint32_t *wmask = reinterpret_cast<uint32_t *>(scratch + CombScratch::wmask_off(N));
+  {
+    uint32_t run = 0;
+    for (int j0 = 0; j0 <= N; j0 += 32) {
+      const int j = j0 + lane;
+      const bool below = j < N && bin_key(Pw, j) < key_lo;
+      const uint32_t b = __ballot_sync(0xffffffffu, below);
+      if (j <= N) preb[j] = (uint16_t)(run + __popc(b & lanemask_lt()));
+      run += __popc(b);
+    }
+  }
   for (int c = d + lane; c <= N - 1 - d; c += 32) {
     float mx = Pw[c - d];
     for (int i = 1; i <= 2 * d; ++i) mx = fmaxf(mx, Pw[c - d + i]);
     wmax[c] = mx;
   }
-  {
-    uint32_t run = 0;
-    const int nwd = CombScratch::words(N);
-    for (int w = 0; w < nwd; ++w) {
-      const int j = w * 32 + lane;
-      const bool below = j < N && bin_key(Pw, j) < key_lo;
-      const uint32_t b = __ballot_sync(0xffffffffu, below);
-      if (lane == 0) {
-        bwords[w] = b;
-        bbase[w] = run;
-      }
-      run += __popc(b);
-    }
+  for (int i = lane; i < N * NW; i += 32) wmask[i] = 0;
+  __syncwarp();
+  for (int b = lane; b < bw; b += 32) {
+    const int jb = bandj[b];
+    for (int c = max(0, jb - d); c <= min(N - 1, jb + d); ++c)
+      atomicOr(&wmask[c * NW + (b >> 5)], 1u << (b & 31));
   }
   __syncwarp();
 
-  // ---- Eq. 8 for every candidate, then the exact Eq. 9-10 only where the
-  // bounds v_lo <= B(w) <= v_hi leave w a chance to be the maximum.
-  float nmax = 0.f;
-  for (int w = cc.w_lo + lane; w <= cc.w_hi; w += 32) {
-    const int mv = min(cc.M, (N - 1 - d) / w);
-    nmax = fmaxf(nmax, comb_nw(wmax, w, mv));
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) nmax = fmaxf(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
-  const float lb_max = snr_of(nmax, v_hi);
-  const float pre = (v_lo > 0.f && v_hi > 0.f) ? __fmul_rn(__fdiv_rn(v_lo, v_hi), 0.999f) : 0.f;
-  float best = -1.f;
+  // ---- Eq. 8-10 for every candidate fundamental, one candidate per lane
+  float best = 0.f;
   int bestw = -1;
-  for (int w0 = cc.w_lo; w0 <= cc.w_hi; w0 += 32) {
-    const int wl = w0 + lane;
-    float nwl = 0.f;
-    bool surv = false;
-    if (wl <= cc.w_hi) {
-      const int mv = min(cc.M, (N - 1 - d) / wl);
-      nwl = comb_nw(wmax, wl, mv);
-      if (nwl >= __fmul_rn(nmax, pre)) surv = !(snr_of(nwl, v_lo) < lb_max);
-    }
-    uint32_t sb = __ballot_sync(0xffffffffu, surv);
-    while (sb) {
-      const int src = __ffs(sb) - 1;
-      sb &= sb - 1;
-      const int w = w0 + src;
-      const float nw = __shfl_sync(0xffffffffu, nwl, src);
-      const int mv = min(cc.M, (N - 1 - d) / w);
-      int h, below;
-      if (w >= 2 * d + 1) {
-        h = mv * (2 * d + 1);
-        int bl = 0;
-        for (int m = lane + 1; m <= mv; m += 32) {
-          const int c = m * w;
-          bl += below_before(bwords, bbase, c + d + 1) - below_before(bwords, bbase, c - d);
-        }
+  const int L = N - 1 - d;
+  for (int w = cc.w_lo + lane; w <= cc.w_hi; w += 32) {
+    // M_valid = min(M, floor(L / w)) without an integer division
+    int mv = __float2int_rz(__fdiv_rz((float)L, (float)w));
+    if ((mv + 1) * w <= L) ++mv;
+    if (mv * w > L) --mv;
+    mv = min(mv, cc.M);
+    float s = 0.f;
+    uint32_t mask[NW];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) bl += __shfl_xor_sync(0xffffffffu, bl, o);
-        below = bl;
-      } else {
-        h = (mv - 1) * w + 2 * d + 1;
-        below = below_before(bwords, bbase, mv * w + d + 1) - below_before(bwords, bbase, w - d);
-      }
-      const int c = N - h;
-      if (c <= 0) continue;
-      uint32_t mask[NW];
+    for (int q = 0; q < NW; ++q) mask[q] = 0;
+    int below = 0, c0 = 0;
+    for (int m = 1; m <= mv; ++m) {
+      c0 += w;
+      s = __fadd_rn(s, wmax[c0]);
+#pragma unroll
+      for (int q = 0; q < NW; ++q) mask[q] |= wmask[c0 * NW + q];
+      below += (int)preb[c0 + d + 1] - (int)preb[c0 - d];
+    }
+    int h;
+    if (w >= 2 * d + 1) {
+      h = mv * (2 * d + 1);
+    } else {  // overlapping windows: their union is one contiguous range
+      h = (mv - 1) * w + 2 * d + 1;
+      below = (int)preb[mv * w + d + 1] - (int)preb[w - d];
+    }
+    const int c = N - h;
+    if (c <= 0) continue;
+    const float nw = ((mv & (mv - 1)) == 0) ? __fmul_rn(s, 1.0f / (float)mv)
+                                            : __fdiv_rn(s, (float)mv);
+    const int base = lo_r - below;
+    float v[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      int t = (k == 0 ? (c - 1) / 2 : c / 2) - base;
+      int pos = -1;
 #pragma unroll
       for (int q = 0; q < NW; ++q) {
-        const int b = q * 32 + lane;
-        bool inside = false;
-        if (b < bw) {
-          const int jb = bandj[b];
-          if (w >= 2 * d + 1) {
-            const int m = (jb + d) / w;
-            inside = m >= 1 && m <= mv && jb + d - m * w <= 2 * d;
-          } else {
-            inside = jb >= w - d && jb <= mv * w + d;
-          }
+        if (pos < 0) {
+          const uint32_t free_bits = ~mask[q];
+          const int nfree = __popc(free_bits);
+          if (t >= 0 && t < nfree) pos = q * 32 + (int)__fns(free_bits, 0, t + 1);
+          else t -= nfree;
         }
-        mask[q] = __ballot_sync(0xffffffffu, inside);
       }
-      const int base = lo_r - below;
-      float v[2];
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        int t = (k == 0 ? (c - 1) / 2 : c / 2) - base;
-        int pos = -1;
-#pragma unroll
-        for (int q = 0; q < NW; ++q) {
-          if (pos < 0) {
-            const uint32_t free_bits = ~mask[q];
-            const int nfree = __popc(free_bits);
-            if (t >= 0 && t < nfree) pos = q * 32 + (int)__fns(free_bits, 0, t + 1);
-            else t -= nfree;
-          }
-        }
-        if (pos < 0 || pos >= bw) {
-          pos = 0;
-          bad = true;
-        }
-        v[k] = bandv[pos];
+      if (pos < 0 || pos >= bw) {
+        pos = 0;
+        bad = true;
       }
-      const float B = (c & 1) ? v[0] : __fmul_rn(__fadd_rn(v[0], v[1]), 0.5f);
-      const float snr = snr_of(nw, B);
-      if (bestw < 0 || snr > best) {
-        best = snr;
-        bestw = w;
-      }
+      v[k] = bandv[pos];
+    }
+    const float B = (c & 1) ? v[0] : __fmul_rn(__fadd_rn(v[0], v[1]), 0.5f);
+    const float snr = snr_of(nw, B);
+    if (bestw < 0 || snr > best) {
+      best = snr;
+      bestw = w;
     }
   }
-  if (bestw < 0) bad = true;  // the maximiser always survives the bounds
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int ow = __shfl_xor_sync(0xffffffffu, bestw, o);
+    if (ow >= 0 && (bestw < 0 || ob > best || (ob == best && ow < bestw))) {
+      best = ob;
+      bestw = ow;
+    }
+  }
   out.bad = __any_sync(0xffffffffu, bad) ? 1 : 0;
   out.snr = bestw >= 0 ? best : 0.f;
   out.w = bestw;
