@@ -260,6 +260,33 @@ ddhf_status ddhf_export_scores(ddhf_ctx *ctx, int32_t slot, uint32_t *active, fl
 ddhf_status ddhf_enable_stage_timing(ddhf_ctx *ctx, int32_t enable);
 ddhf_status ddhf_stage_times(ddhf_ctx *ctx, float *out_ms);
 
+/* Soft comb score and its gradients for the differentiation pattern (not in
+ * the paper; built on Eq. 6 and the comb of Eq. 8-10). For each listed pixel
+ * a (pixels[n_px]: pixel keys y*W+x of the last binned window) with
+ * fundamental f0[a] (Hz):
+ *   f_hq = h f0 + q delta_hz,  h = 1..n_h (<= 8), q = -Q..Q (Q <= 8)
+ *   G_hq = exp(-(q delta)^2 / (2 sigma_h^2)),  Z_h = sum_q G_hq
+ *   S[a] = sum_h w_h (sum_q G_hq P_a(f_hq) / Z_h) / B[a]
+ * where P_a(f) = |sum_k p_k exp(-2 pi i f (tau_k - tau_c_us) 1e-6)|^2 is Eq. 6
+ * at a real frequency (exact integer-mHz phase plus a sub-mHz remainder) and
+ * B[a] > 0 a constant background (e.g. ddhf_spectrum_median of the grid
+ * spectrum). w, sigma: [n_h] device floats.
+ * Forward (grad_S == NULL): writes S[n_px].
+ * Backward (grad_S != NULL, S ignored): with g = grad_S,
+ *   grad_f0[a] = g[a] dS_a/df0,  grad_w[h] = sum_a g[a] dS_a/dw_h,
+ *   grad_sigma[h] = sum_a g[a] dS_a/dsigma_h,
+ * using dP/df = 2 Re(conj F dF/df); sums over pixels in a fixed order. */
+ddhf_status ddhf_softcomb(ddhf_ctx *ctx, int64_t n_px, const uint32_t *pixels, const float *f0,
+                          int32_t n_h, int32_t Q, double delta_hz, double tau_c_us,
+                          const float *w, const float *sigma, const float *B, float *S,
+                          const float *grad_S, float *grad_f0, float *grad_w, float *grad_sigma,
+                          ddhf_stream stream);
+
+/* Median of each spectrum row P[rows][n_bins] (the mean of the two middle
+ * values for an even count, as in Eq. 9-10), exact: median[rows]. */
+ddhf_status ddhf_spectrum_median(ddhf_ctx *ctx, const float *P, int64_t rows, float *median,
+                                 ddhf_stream stream);
+
 /* Spectra without any device allocation. The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory while
  * running (for example an embedded real-time detector whose memory is all

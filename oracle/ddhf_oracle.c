@@ -133,7 +133,9 @@ void oracle_ndft_at(int64_t n, const int64_t *tau, const int8_t *pol,
     for (int64_t k = 0; k < n; ++k) {
       /* cycles = f * (tau - tau_c) * 1e-6, split into the exact integer part
          a*tau mod 1e9 (in 1e-9 cycles) and the small remainders. */
-      int64_t r = phase_residue(a, tau[k], 1000000000LL);
+      int64_t am = a % 1000000000LL; /* residue of any sign, into [0, 1e9) */
+      if (am < 0) am += 1000000000LL;
+      int64_t r = phase_residue(am, tau[k], 1000000000LL);
       double cyc = (double)r * 1e-9 + fr * (double)tau[k] * 1e-6 - f * tau_c * 1e-6;
       double theta = 2.0 * M_PI * cyc;
       double c = cos(theta), s = sin(theta);

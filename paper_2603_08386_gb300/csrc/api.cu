@@ -76,6 +76,7 @@ void free_all(Ctx *c) {
   F(c->box_root);
   F(c->box_tmp);
   F(c->flags);
+  F(c->soft_part);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   c->graph_exec = nullptr;
   for (auto &e : c->stage_ev)
@@ -331,6 +332,7 @@ ddhf_status ddhf_create(int32_t W, int32_t H, const ddhf_grid *grid, const ddhf_
   A(c->box_root, npx);
   A(c->box_tmp, 15 * npx);
   A(c->flags, 1);
+  A(c->soft_part, 16 * npx + 16);
 #undef A
   if (st == DDHF_OK) {
     cudaMemset(c->qctl, 0, 16 * sizeof(uint32_t));

@@ -100,6 +100,7 @@ struct Ctx {
   int32_t *box_root = nullptr;   // [npx]
   int32_t *box_tmp = nullptr;    // [npx * 6]
   uint32_t *flags = nullptr;     // [1] DDHF_FLAG_* bits
+  float *soft_part = nullptr;    // [16 * npx + 16] soft-comb gradient partials
   CombConst comb{};
   GridConst gconst{};
   cudaStream_t last_stream = nullptr;

@@ -90,6 +90,9 @@ SIGNATURES = {
     "ddhf_enable_stage_timing": (_I32, [_VP, _I32]),
     "ddhf_stage_times": (_I32, [_VP, ctypes.POINTER(ctypes.c_float)]),
     "ddhf_last_error": (ctypes.c_char_p, [_VP]),
+    "ddhf_softcomb": (_I32, [_VP, _I64, _VP, _VP, _I32, _I32, ctypes.c_double, ctypes.c_double,
+                             _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "ddhf_spectrum_median": (_I32, [_VP, _VP, _I64, _VP, _VP]),
     "ddhf_power_spectrum_noalloc": (_I32, [ctypes.POINTER(ddhf_grid), _VP, _VP, _I64, _VP, _I64,
                                            _VP, _I64, _VP]),
 }
@@ -248,6 +251,45 @@ def ddhf_power_spectrum_noalloc(grid, offsets, ev, n_events, active, n_active, P
     _check(load().ddhf_power_spectrum_noalloc(ctypes.byref(grid), _ptr(offsets), _ptr(ev),
                                               int(n_events), _ptr(active), int(n_active),
                                               _ptr(P), int(cap_px), _stream(stream)))
+
+
+def ddhf_softcomb(ctx, pixels, f0, n_h, Q, delta_hz, tau_c_us, w, sigma, B, S=None,
+                  grad_S=None, grad_f0=None, grad_w=None, grad_sigma=None, stream=None):
+    _check(load().ddhf_softcomb(ctx, int(pixels.numel()), _ptr(pixels), _ptr(f0), int(n_h), int(Q),
+                                float(delta_hz), float(tau_c_us), _ptr(w), _ptr(sigma), _ptr(B),
+                                _ptr(S), _ptr(grad_S), _ptr(grad_f0), _ptr(grad_w),
+                                _ptr(grad_sigma), _stream(stream)), ctx)
+
+
+def ddhf_spectrum_median(ctx, P, rows, median, stream=None):
+    _check(load().ddhf_spectrum_median(ctx, _ptr(P), int(rows), _ptr(median), _stream(stream)), ctx)
+
+
+class SoftComb(torch.autograd.Function):
+    """Soft comb score S per pixel as a differentiable function of the
+    per-pixel fundamentals f0 and the shared harmonic weights w and widths
+    sigma; forward and backward both run in the library's kernels
+    (ddhf_softcomb). B (background) is held constant."""
+
+    @staticmethod
+    def forward(ctx_, f0, w, sigma, handle, pixels, B, Q, delta_hz, tau_c_us):
+        f0c, wc, sc = f0.contiguous(), w.contiguous(), sigma.contiguous()
+        S = torch.empty_like(f0c)
+        ddhf_softcomb(handle, pixels, f0c, wc.numel(), Q, delta_hz, tau_c_us, wc, sc, B, S=S)
+        ctx_.save_for_backward(f0c, wc, sc)
+        ctx_.extra = (handle, pixels, B, Q, delta_hz, tau_c_us)
+        return S
+
+    @staticmethod
+    def backward(ctx_, gS):
+        f0c, wc, sc = ctx_.saved_tensors
+        handle, pixels, B, Q, delta_hz, tau_c_us = ctx_.extra
+        g_f0 = torch.empty_like(f0c)
+        g_w = torch.empty_like(wc)
+        g_s = torch.empty_like(sc)
+        ddhf_softcomb(handle, pixels, f0c, wc.numel(), Q, delta_hz, tau_c_us, wc, sc, B,
+                      grad_S=gS.contiguous(), grad_f0=g_f0, grad_w=g_w, grad_sigma=g_s)
+        return g_f0, g_w, g_s, None, None, None, None, None, None
 
 
 def ddhf_get_stats(ctx, raise_on_flags=True):

@@ -462,3 +462,14 @@ def test_classify_composition_on_small_scene():
             assert (c["snr"][i], c["w"][i]) == (pytest.approx(sn), w)
     assert np.all(b["counts"][c["active"]] >= 6)
     assert int((b["counts"] >= 6).sum()) == len(c["active"])
+
+
+def test_ndft_at_negative_frequency_is_conjugate():
+    # real polarities: F(-f) = conj(F(f)); pins the residue of a negative mHz count
+    rng = np.random.default_rng(17)
+    tau, pol = _rand_events(rng, 25)
+    f = np.array([0.5, 13.25, 151.0007])
+    Fp, Dp = oracle.ndft_at(tau, pol, f)
+    Fm, Dm = oracle.ndft_at(tau, pol, -f)
+    np.testing.assert_allclose(Fm, np.conj(Fp), atol=1e-9)
+    np.testing.assert_allclose(Dm, -np.conj(Dp), atol=1e-6)  # D(-f) = -conj(D(f))
