@@ -141,15 +141,28 @@ typedef struct {
 #define DDHF_FORM_F64 5
 
 /* Launch tuning of the persistent BLOCKED kernel (chosen by the autotuner).
- *  heavy_min   pixels with at least this many events are processed by a
- *              whole thread block (events split over its warps), the others
+ *  heavy_min   pixels with at least this many events (>= 32) are processed by
+ *              a whole thread block (events split over its warps), the others
  *              by one warp each;
  *  warps_per_block  warps per thread block (2, 4 or 8);
- *  blocks_per_sm    resident blocks per SM used to size the persistent grid. */
+ *  blocks_per_sm    resident blocks per SM used to size the persistent grid
+ *                   (0 = as many as fit);
+ *  rows_per_lane    32-bin rows held per lane (1, 2, 4, 6 or 8; 0 = chosen
+ *                   from n_bins): a pass covers 4 * rows_per_lane rows, and
+ *                   every pass re-seeds the phasor rows exactly;
+ *  fuse             1: ddhf_detect / ddhf_detect_batch score each spectrum in
+ *                   the kernel that computes it (spectra stay on chip); 0:
+ *                   per window, a spectrum kernel writes a context-owned
+ *                   buffer that a separate comb kernel reads (more warps per
+ *                   SM for the latency-bound comb). Same results either way.
+ * Different tunings give spectra that agree within the FP32 rounding of the
+ * summation order; each tuning is deterministic. */
 typedef struct {
   int32_t heavy_min;
   int32_t warps_per_block;
   int32_t blocks_per_sm;
+  int32_t rows_per_lane;
+  int32_t fuse;
   int32_t reserved;
 } ddhf_tuning;
 
@@ -251,12 +264,15 @@ ddhf_status ddhf_export_scores(ddhf_ctx *ctx, int32_t slot, uint32_t *active, fl
                                float *snr, int32_t *f0_bin, int64_t *counts,
                                ddhf_stream stream);
 
-/* Tracing: when enable is nonzero, CUDA events bracket the three stages of
- * every later ddhf_detect / ddhf_detect_batch call (also inside a captured
- * graph; enabling or disabling drops a cached graph). ddhf_stage_times()
- * waits for the last recorded call and writes out_ms[3] (host) = device time
- * of {binning of all windows, fused NDFT + SF + comb kernel, labels + boxes}
- * in milliseconds. Returns DDHF_ERR_STATE if nothing was recorded. */
+/* Tracing: when enable is nonzero, CUDA events bracket the stages of every
+ * later ddhf_detect / ddhf_detect_batch call (also inside a captured graph,
+ * as external event nodes; enabling or disabling drops a cached graph).
+ * ddhf_stage_times() waits for the last recorded call and writes out_ms[5]
+ * (host), device milliseconds summed over the call's windows:
+ *   [0] binning, [1] classification (NDFT + SF + comb), [2] labels + boxes,
+ *   [3] spectrum kernels and [4] comb kernels of the unfused path (0 when
+ *   fused, where [1] is the single fused kernel).
+ * Returns DDHF_ERR_STATE if nothing was recorded. */
 ddhf_status ddhf_enable_stage_timing(ddhf_ctx *ctx, int32_t enable);
 ddhf_status ddhf_stage_times(ddhf_ctx *ctx, float *out_ms);
 

@@ -77,10 +77,14 @@ void free_all(Ctx *c) {
   F(c->box_tmp);
   F(c->flags);
   F(c->soft_part);
+  F(c->pbuf);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   c->graph_exec = nullptr;
   for (auto &e : c->stage_ev)
     if (e) cudaEventDestroy(e);
+  for (auto &e : c->win_ev)
+    if (e) cudaEventDestroy(e);
+  c->win_ev.clear();
 }
 
 void drop_graph(Ctx *c) {
@@ -175,26 +179,48 @@ ddhf_status bin_into(Ctx *c, int slot, const int16_t *x, const int16_t *y, const
 
 // Stage event: an external event node while the stream is being captured into
 // a graph, a plain record otherwise.
-cudaError_t record_stage(Ctx *c, int i, cudaStream_t s) {
+cudaError_t record_event(cudaEvent_t ev, cudaStream_t s) {
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   cudaError_t e = cudaStreamIsCapturing(s, &cs);
   if (e != cudaSuccess) return e;
   if (cs == cudaStreamCaptureStatusActive)
-    return cudaEventRecordWithFlags(c->stage_ev[i], s, cudaEventRecordExternal);
-  return cudaEventRecord(c->stage_ev[i], s);
+    return cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal);
+  return cudaEventRecord(ev, s);
 }
+
+cudaError_t record_stage(Ctx *c, int i, cudaStream_t s) { return record_event(c->stage_ev[i], s); }
 
 ddhf_status run_detect(Ctx *c, const ddhf_window *wins, int nw, ddhf_box *boxes, int32_t cap,
                        int32_t *n_boxes_dev, uint8_t *masks_out, cudaStream_t s) {
   if (c->timing) DDHF_CUDA_TRY(c, record_stage(c, 0, s));
-  DDHF_CUDA_TRY(c, cudaMemsetAsync(c->qctl, 0, sizeof(uint32_t), s));  // heavy count
-  for (int w = 0; w < nw; ++w) {
-    const ddhf_window &W = wins[w];
-    DDHF_CUDA_TRY(c, cudaMemsetAsync(c->slots[w].mask, 0, c->npx, s));
-    DDHF_TRY(bin_into(c, w, W.x, W.y, W.t_us, W.p, W.n, W.t0_us, W.window_us, s));
+  const bool fused = c->tuning.fuse != 0 || !c->pbuf;
+  if (fused) {
+    DDHF_CUDA_TRY(c, cudaMemsetAsync(c->qctl, 0, sizeof(uint32_t), s));  // heavy count
+    for (int w = 0; w < nw; ++w) {
+      const ddhf_window &W = wins[w];
+      DDHF_CUDA_TRY(c, cudaMemsetAsync(c->slots[w].mask, 0, c->npx, s));
+      DDHF_TRY(bin_into(c, w, W.x, W.y, W.t_us, W.p, W.n, W.t0_us, W.window_us, s));
+    }
+    if (c->timing) DDHF_CUDA_TRY(c, record_stage(c, 1, s));
+    DDHF_TRY(launch_fused(c, nw, true, nullptr, 0, s));
+  } else {
+    // per window: binning (own heavy list), spectra into the context buffer, comb
+    for (int w = 0; w < nw; ++w) {
+      const ddhf_window &W = wins[w];
+      cudaEvent_t *we = c->timing ? &c->win_ev[4 * w] : nullptr;
+      if (we) DDHF_CUDA_TRY(c, record_event(we[0], s));
+      DDHF_CUDA_TRY(c, cudaMemsetAsync(c->qctl, 0, sizeof(uint32_t), s));
+      DDHF_TRY(bin_into(c, w, W.x, W.y, W.t_us, W.p, W.n, W.t0_us, W.window_us, s));
+      if (we) DDHF_CUDA_TRY(c, record_event(we[1], s));
+      Slot &sl = c->slots[w];
+      DDHF_TRY(launch_spectrum_slot(c, w, c->pbuf, c->npx, s));
+      if (we) DDHF_CUDA_TRY(c, record_event(we[2], s));
+      DDHF_TRY(launch_comb(c, c->pbuf, c->npx, sl.log_sf, sl.snr, sl.f0, sl.mask, s, w));
+      if (we) DDHF_CUDA_TRY(c, record_event(we[3], s));
+    }
   }
-  if (c->timing) DDHF_CUDA_TRY(c, record_stage(c, 1, s));
-  DDHF_TRY(launch_fused(c, nw, true, nullptr, 0, s));
+  c->timing_fused = fused;
+  c->timing_windows = nw;
   if (c->timing) DDHF_CUDA_TRY(c, record_stage(c, 2, s));
   for (int w = 0; w < nw; ++w) {
     Slot &sl = c->slots[w];
@@ -272,7 +298,7 @@ ddhf_status ddhf_create(int32_t W, int32_t H, const ddhf_grid *grid, const ddhf_
   c->params = *params;
   c->max_events = max_events;
   c->max_windows = max_windows;
-  c->tuning = ddhf_tuning{1024, 4, 0, 0};
+  c->tuning = ddhf_tuning{1024, 4, 0, 0, 1, 0};
   cudaError_t e = cudaGetDevice(&c->device);
   if (e == cudaSuccess)
     e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
@@ -333,6 +359,7 @@ ddhf_status ddhf_create(int32_t W, int32_t H, const ddhf_grid *grid, const ddhf_
   A(c->box_tmp, 15 * npx);
   A(c->flags, 1);
   A(c->soft_part, 16 * npx + 16);
+  if (grid->n_bins <= 4096) A(c->pbuf, npx * (int64_t)grid->n_bins);
 #undef A
   if (st == DDHF_OK) {
     cudaMemset(c->qctl, 0, 16 * sizeof(uint32_t));
@@ -362,9 +389,12 @@ ddhf_status ddhf_destroy(ddhf_ctx *h) {
 
 ddhf_status ddhf_set_tuning(ddhf_ctx *h, const ddhf_tuning *t) {
   if (!h || !t) return DDHF_ERR_INVALID_ARG;
+  const int r = t->rows_per_lane;
   if (t->heavy_min < 32 || (t->warps_per_block != 2 && t->warps_per_block != 4 &&
                             t->warps_per_block != 8) ||
-      t->blocks_per_sm < 0 || t->blocks_per_sm > 32)
+      t->blocks_per_sm < 0 || t->blocks_per_sm > 32 ||
+      !(r == 0 || r == 1 || r == 2 || r == 4 || r == 6 || r == 8) ||
+      (t->fuse != 0 && t->fuse != 1))
     return fail(&h->c, DDHF_ERR_INVALID_ARG, "tuning out of range");
   h->c.tuning = *t;
   drop_graph(&h->c);
@@ -376,6 +406,8 @@ ddhf_status ddhf_enable_stage_timing(ddhf_ctx *h, int32_t enable) {
   Ctx *c = &h->c;
   if (enable && !c->stage_ev[0]) {
     for (auto &e : c->stage_ev) DDHF_CUDA_TRY(c, cudaEventCreate(&e));
+    c->win_ev.assign(4 * (size_t)c->max_windows, nullptr);
+    for (auto &e : c->win_ev) DDHF_CUDA_TRY(c, cudaEventCreate(&e));
   }
   if ((bool)enable != c->timing) drop_graph(c);
   c->timing = enable != 0;
@@ -388,8 +420,24 @@ ddhf_status ddhf_stage_times(ddhf_ctx *h, float *out_ms) {
   Ctx *c = &h->c;
   if (!c->timing || !c->timing_recorded) return fail(c, DDHF_ERR_STATE, "no timed detection");
   DDHF_CUDA_TRY(c, cudaEventSynchronize(c->stage_ev[3]));
-  for (int i = 0; i < 3; ++i)
-    DDHF_CUDA_TRY(c, cudaEventElapsedTime(&out_ms[i], c->stage_ev[i], c->stage_ev[i + 1]));
+  for (int i = 0; i < 5; ++i) out_ms[i] = 0.f;
+  if (c->timing_fused) {
+    for (int i = 0; i < 3; ++i)
+      DDHF_CUDA_TRY(c, cudaEventElapsedTime(&out_ms[i], c->stage_ev[i], c->stage_ev[i + 1]));
+  } else {
+    for (int w = 0; w < c->timing_windows; ++w) {
+      float b, sp, cb;
+      const cudaEvent_t *we = &c->win_ev[4 * w];
+      DDHF_CUDA_TRY(c, cudaEventElapsedTime(&b, we[0], we[1]));
+      DDHF_CUDA_TRY(c, cudaEventElapsedTime(&sp, we[1], we[2]));
+      DDHF_CUDA_TRY(c, cudaEventElapsedTime(&cb, we[2], we[3]));
+      out_ms[0] += b;
+      out_ms[3] += sp;
+      out_ms[4] += cb;
+    }
+    out_ms[1] = out_ms[3] + out_ms[4];
+    DDHF_CUDA_TRY(c, cudaEventElapsedTime(&out_ms[2], c->stage_ev[2], c->stage_ev[3]));
+  }
   return DDHF_OK;
 }
 

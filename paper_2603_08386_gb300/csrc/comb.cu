@@ -37,8 +37,8 @@ __global__ void k_comb(const float *__restrict__ P, int64_t cap_px, const uint32
 }  // namespace
 
 ddhf_status launch_comb(Ctx *c, const float *P, int64_t cap_px, float *log_sf, float *snr,
-                        int32_t *f0, uint8_t *mask, cudaStream_t s) {
-  const Slot &sl = c->slots[0];
+                        int32_t *f0, uint8_t *mask, cudaStream_t s, int slot) {
+  const Slot &sl = c->slots[slot];
   const int nw = (c->comb.bw + 31) / 32;
   const int wpb = 4;
   const int warp_bytes = ((c->grid.n_bins * 4 + 15) & ~15) +

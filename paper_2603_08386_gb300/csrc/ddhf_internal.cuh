@@ -101,6 +101,7 @@ struct Ctx {
   int32_t *box_tmp = nullptr;    // [npx * 6]
   uint32_t *flags = nullptr;     // [1] DDHF_FLAG_* bits
   float *soft_part = nullptr;    // [16 * npx + 16] soft-comb gradient partials
+  float *pbuf = nullptr;         // [npx * n_bins] spectra of one window (unfused detection)
   CombConst comb{};
   GridConst gconst{};
   cudaStream_t last_stream = nullptr;
@@ -109,7 +110,10 @@ struct Ctx {
   // stage timing (tracing)
   bool timing = false;
   bool timing_recorded = false;
+  bool timing_fused = true;
+  int timing_windows = 0;
   cudaEvent_t stage_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  std::vector<cudaEvent_t> win_ev;  // 4 per window (unfused path)
   // graph cache of ddhf_detect_batch
   int64_t graph_kernels = 0;
   cudaGraphExec_t graph_exec = nullptr;
@@ -163,8 +167,9 @@ ddhf_status launch_scan_u32(Ctx *c, const uint32_t *in, uint32_t *out, int64_t n
                             cudaStream_t s);
 // ndft.cu
 ddhf_status launch_spectrum(Ctx *c, int form, float *P, int64_t cap_px, cudaStream_t s);
+ddhf_status launch_spectrum_slot(Ctx *c, int slot, float *P, int64_t cap_px, cudaStream_t s);
 ddhf_status launch_comb(Ctx *c, const float *P, int64_t cap_px, float *log_sf, float *snr,
-                        int32_t *f0, uint8_t *mask, cudaStream_t s);
+                        int32_t *f0, uint8_t *mask, cudaStream_t s, int slot = 0);
 ddhf_status launch_fused(Ctx *c, int n_slots, bool write_p, float *P, int64_t cap_px,
                          cudaStream_t s);
 void set_bin_attributes();

@@ -175,6 +175,7 @@ __device__ __forceinline__ void finalize_tile(const Acc<TB> &acc, float *Pw, int
 
 struct BlockedArgs {
   const SlotView *views;
+  int slot0;                 // first slot of the light-pixel range
   int n_slots;
   int64_t npx;
   const uint64_t *heavy;     // heavy work items (slot << 32 | active index)
@@ -316,8 +317,8 @@ __global__ void k_blocked(BlockedArgs A) {
     for (int q = 0; q < kGrab; ++q) {
       const int64_t vi = (int64_t)v0 + q;
       if (vi >= total) break;
-      const int slot = (int)(vi / A.npx);
-      const int64_t a = vi - (int64_t)slot * A.npx;
+      const int slot = A.slot0 + (int)(vi / A.npx);
+      const int64_t a = vi - (int64_t)(slot - A.slot0) * A.npx;
       const SlotView v = A.views[slot];
       if (a >= (int64_t)v.counters[2]) continue;
       const uint32_t key = v.active[a];
@@ -355,9 +356,11 @@ int blocked_warp_bytes(const Ctx *c, bool fused, int NW, int *pw_offset) {
 }
 
 template <int TB, int NW, bool FUSED>
-ddhf_status launch_blocked_t(Ctx *c, int n_slots, float *P, int64_t cap_px, cudaStream_t s) {
+ddhf_status launch_blocked_t(Ctx *c, int n_slots, float *P, int64_t cap_px, cudaStream_t s,
+                             int slot0 = 0) {
   BlockedArgs A;
   A.views = c->d_views;
+  A.slot0 = slot0;
   A.n_slots = n_slots;
   A.npx = c->npx;
   A.heavy = c->work;
@@ -390,15 +393,17 @@ ddhf_status launch_blocked_t(Ctx *c, int n_slots, float *P, int64_t cap_px, cuda
 }
 
 template <bool FUSED>
-ddhf_status launch_blocked_any(Ctx *c, int n_slots, float *P, int64_t cap_px, cudaStream_t s) {
+ddhf_status launch_blocked_any(Ctx *c, int n_slots, float *P, int64_t cap_px, cudaStream_t s,
+                               int slot0 = 0) {
   const int nbr = c->gconst.nbr;
   int tb = std::min(8, (nbr + 3) / 4);
   tb = tb <= 2 ? tb : tb <= 4 ? 4 : tb <= 6 ? 6 : 8;
+  if (c->tuning.rows_per_lane > 0) tb = c->tuning.rows_per_lane;
   const int nw = (c->comb.bw + 31) / 32;
 #define DDHF_TB_CASE(T)                                                           \
   case T:                                                                         \
-    if (!FUSED || nw <= 1) return launch_blocked_t<T, 1, FUSED>(c, n_slots, P, cap_px, s); \
-    return launch_blocked_t<T, 8, FUSED>(c, n_slots, P, cap_px, s);
+    if (!FUSED || nw <= 1) return launch_blocked_t<T, 1, FUSED>(c, n_slots, P, cap_px, s, slot0); \
+    return launch_blocked_t<T, 8, FUSED>(c, n_slots, P, cap_px, s, slot0);
   switch (tb) {
     DDHF_TB_CASE(1)
     DDHF_TB_CASE(2)

@@ -63,7 +63,8 @@ class ddhf_stats(ctypes.Structure):
 
 class ddhf_tuning(ctypes.Structure):
     _fields_ = [("heavy_min", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("blocks_per_sm", ctypes.c_int32), ("rows_per_lane", ctypes.c_int32),
+                ("fuse", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 # exported symbol -> (restype, argtypes)
@@ -170,8 +171,10 @@ def ddhf_destroy(ctx):
     _check(load().ddhf_destroy(ctx))
 
 
-def ddhf_set_tuning(ctx, heavy_min=1024, warps_per_block=4, blocks_per_sm=0):
-    t = ddhf_tuning(int(heavy_min), int(warps_per_block), int(blocks_per_sm), 0)
+def ddhf_set_tuning(ctx, heavy_min=1024, warps_per_block=4, blocks_per_sm=0, rows_per_lane=0,
+                    fuse=1):
+    t = ddhf_tuning(int(heavy_min), int(warps_per_block), int(blocks_per_sm), int(rows_per_lane),
+                    int(fuse), 0)
     _check(load().ddhf_set_tuning(ctx, ctypes.byref(t)), ctx)
 
 
@@ -179,7 +182,7 @@ def ddhf_get_tuning(ctx):
     t = ddhf_tuning()
     _check(load().ddhf_get_tuning(ctx, ctypes.byref(t)), ctx)
     return dict(heavy_min=t.heavy_min, warps_per_block=t.warps_per_block,
-                blocks_per_sm=t.blocks_per_sm)
+                blocks_per_sm=t.blocks_per_sm, rows_per_lane=t.rows_per_lane, fuse=t.fuse)
 
 
 def ddhf_bin_events(ctx, x, y, t, p, n, t0, window_us, stream=None):
@@ -237,9 +240,10 @@ def ddhf_enable_stage_timing(ctx, enable=True):
 
 
 def ddhf_stage_times(ctx):
-    """Device milliseconds of {binning, fused classify, labels + boxes} of the
-    last timed detection call."""
-    out = (ctypes.c_float * 3)()
+    """Device milliseconds of {binning, classification, labels + boxes,
+    spectrum kernels, comb kernels} of the last timed detection call (the last
+    two are 0 on the fused path)."""
+    out = (ctypes.c_float * 5)()
     _check(load().ddhf_stage_times(ctx, out), ctx)
     return [float(v) for v in out]
 

@@ -315,6 +315,16 @@ def test_fused_equals_unfused_bitwise():
         assert torch.equal(out["f0_bin"], sc["f0_bin"])
         assert torch.equal(out["snr"].view(torch.int32), sc["snr"].view(torch.int32))
         assert torch.equal(out["log_sf"].view(torch.int32), sc["log_sf"].view(torch.int32))
+        # the unfused detection path (spectrum kernel + comb kernel per window)
+        c2 = ctx_for(s, heavy_min=heavy_min, fuse=0)
+        bx2, nb2, mask2 = c2.detect(x, y, t, p, s.t0, s.window_us, want_mask=True)
+        sc2 = c2.scores()
+        c2.stats()
+        c2.close()
+        assert torch.equal(mask2, mask) and torch.equal(sc2["f0_bin"], sc["f0_bin"])
+        assert torch.equal(sc2["snr"].view(torch.int32), sc["snr"].view(torch.int32))
+        assert int(nb2.item()) == int(nb.item())
+        assert torch.equal(bx2[: int(nb.item())], bx[: int(nb.item())])
 
 
 def test_batch_graph_equals_single_windows():
