@@ -362,185 +362,6 @@ def main():
     else:
         ndft_ms, kern = statistics.mean(spec_ms), "blocked NDFT spectrum kernel (k_blocked<TB,1,0>)"
     achieved = OPS_PER_TERM * terms_step / (ndft_ms * 1e-3) / 1e12
-    line = dict(impl="reference", metric=METRIC, value=v, unit=UNIT, n_gpus=args.gpus,
-                steps=args.steps, warmup=args.warmup, ms_per_step=1e3 * tot_s / args.steps,
-                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
-                data="synthetic",
-                config=dict(workload="C3 1280x720 30 ms windows, ~20M events/window, 750 bins; "
-                                     "oracle on pixel samples"),
-                cpu_baseline=dict(value=v, unit=UNIT, cores=1, kind="oracle", sample=sample),
-                e2e=dict(value=v, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
-    print(json.dumps(line), flush=True)
-
-
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-plain", action="store_true", help="skip the plain-pipeline comparison")
-    ap.add_argument("--no-oracle", action="store_true", help="skip the CPU baseline")
-    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer e2e loop")
-    ap.add_argument("--windows", type=int, default=N_STREAMS * N_WINDOWS,
-                    help="windows per step (default 32; fewer only for profiling cases)")
-    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default tuning)")
-    ap.add_argument("--procs", type=int, default=int(os.environ.get("DDHF_GEN_PROCS", "16")))
-    args = ap.parse_args()
-    if args.impl == "reference":
-        run_reference(args)
-        return
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    # inputs are generated before any CUDA call (spawned workers)
-    wins = generate(rank, max(1, args.procs // max(1, world)), args.windows)
-
-    import torch
-    from paper_2603_08386_gb300 import build, ddhf
-    build.build()
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    W, H = 1280, 720
-    grid = synth.hz_grid(0, 2, 750)
-    nb = grid[3]
-    terms_step = sum(terms_of(w, W, H, nb) for w in wins)
-    events_step = sum(w[6] for w in wins)
-    max_ev = max(w[6] for w in wins)
-    nwin = len(wins)
-    cap = 256
-    ctx = ddhf.Context(W, H, grid, max_events=max_ev, max_windows=nwin)
-    dev = [tuple(torch.from_numpy(a).cuda() for a in w[:4]) for w in wins]
-    wl = [(d[0], d[1], d[2], d[3], w[6], w[4], w[5]) for d, w in zip(dev, wins)]
-    boxes = torch.empty((nwin * cap, 5), dtype=torch.int32, device="cuda")
-    nbox = torch.zeros(nwin, dtype=torch.int32, device="cuda")
-    ddhf.ddhf_enable_stage_timing(ctx.h, True)
-    tuning, tune_note = ddhf.ddhf_get_tuning(ctx.h), "default"
-    if not args.no_tune:
-        # the autotuner times the fused kernel on the first 4 windows of this batch
-        from paper_2603_08386_gb300 import tune
-        k = min(4, nwin)
-        tctx = ddhf.Context(W, H, grid, max_events=max_ev, max_windows=k)
-        tb = torch.empty((k * cap, 5), dtype=torch.int32, device="cuda")
-        tn = torch.zeros(k, dtype=torch.int32, device="cuda")
-        tuning, _ = tune.autotune(tctx, wl[:k], tb, cap, tn)
-        tctx.close()
-        ctx.set_tuning(**tuning)
-        tune_note = f"autotuned on {k} windows"
-
-    def step():
-        ddhf.ddhf_detect_batch(ctx.h, wl, boxes, cap, nbox, None, use_graph=True)
-
-    for _ in range(max(args.warmup, 1)):
-        step()
-    torch.cuda.synchronize()
-    st = ctx.stats()
-    graph_kernels = st["graph_kernels"]
-    # ------------------------------------------------------------ timed region
-    clocks = Clocks(torch.cuda.current_device())
-    clocks.start()
-    time.sleep(0.3)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    fused_ms, bin_ms, box_ms, spec_ms, comb_ms = [], [], [], [], []
-    e0.record()
-    for _ in range(args.steps):
-        step()
-        b_ms, f_ms, x_ms, sp_ms, cb_ms = ddhf.ddhf_stage_times(ctx.h)  # waits for this step
-        bin_ms.append(b_ms)
-        fused_ms.append(f_ms)
-        box_ms.append(x_ms)
-        spec_ms.append(sp_ms)
-        comb_ms.append(cb_ms)
-    e1.record()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    clk = clocks.stop()
-    ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
-    ms_step = ms / args.steps
-    value = job_throughput(terms_step, world, args.steps, ms)
-    st = ctx.stats()
-    # ------------------------------------------------------------ e2e from pinned host memory
-    e2e = None
-    if not args.no_e2e:
-        host = [tuple(torch.from_numpy(a).pin_memory() for a in w[:4]) for w in wins]
-        h2d = sum(sum(a.numel() * a.element_size() for a in hw) for hw in host)
-        hbox = torch.empty((nwin * cap, 5), dtype=torch.int32).pin_memory()
-        hn = torch.empty(nwin, dtype=torch.int32).pin_memory()
-        d2h = hbox.numel() * 4 + hn.numel() * 4
-
-        def e2e_step():
-            for d, hw in zip(dev, host):
-                for dst, src in zip(d, hw):
-                    dst.copy_(src, non_blocking=True)
-            step()
-            hbox.copy_(boxes, non_blocking=True)
-            hn.copy_(nbox, non_blocking=True)
-
-        e2e_step()
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        e2e_steps = max(1, min(args.steps, 5))
-        e0.record()
-        for _ in range(e2e_steps):
-            e2e_step()
-        e1.record()
-        torch.cuda.synchronize()
-        e2e_ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
-        e2e = dict(value=job_throughput(terms_step, world, e2e_steps, e2e_ms), unit=UNIT,
-                   h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h, steps=e2e_steps)
-    # ------------------------------------------------------------ plain per-pixel pipeline
-    plain = None
-    if not args.no_plain:
-        pc = ddhf.Context(W, H, grid, max_events=max_ev, max_windows=1)
-        k = min(4, nwin)
-        P = torch.empty((W * H, nb), dtype=torch.float32, device="cuda")
-        lsf = torch.empty(W * H, device="cuda")
-        snr = torch.empty(W * H, device="cuda")
-        f0 = torch.empty(W * H, dtype=torch.int32, device="cuda")
-        mask = torch.empty(W * H, dtype=torch.uint8, device="cuda")
-        lab = torch.empty(W * H, dtype=torch.int32, device="cuda")
-        pb = torch.empty((cap, 5), dtype=torch.int32, device="cuda")
-        pn = torch.zeros(1, dtype=torch.int32, device="cuda")
-
-        def plain_window(i):
-            d, w = dev[i], wins[i]
-            ddhf.ddhf_bin_events(pc.h, d[0], d[1], d[2], d[3], w[6], w[4], w[5])
-            ddhf.ddhf_power_spectrum(pc.h, ddhf.FORM["recur"], P, W * H)
-            ddhf.ddhf_comb_score(pc.h, P, W * H, lsf, snr, f0, mask)
-            ddhf.ddhf_label(pc.h, mask, lab)
-            ddhf.ddhf_boxes(pc.h, lab, pb, cap, pn)
-
-        plain_window(0)
-        torch.cuda.synchronize()
-        e0.record()
-        for i in range(k):
-            plain_window(i)
-        e1.record()
-        torch.cuda.synchronize()
-        pms = e0.elapsed_time(e1) / k
-        pterms = sum(terms_of(wins[i], W, H, nb) for i in range(k)) / k
-        plain = dict(form="recur, one warp per pixel, per-window launches, spectra in HBM",
-                     ms_per_window=pms, value=pterms / (pms * 1e-3), unit=UNIT,
-                     windows=k)
-        pc.close()
-    # ------------------------------------------------------------ CPU baseline (oracle)
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_oracle:
-        tr, secs, npix = oracle_sample(oracle_bin(wins[0], W, H), W, H, grid, 1200)
-        cpu = dict(value=tr / secs, unit=UNIT, cores=1, kind="oracle",
-                   sample=f"{npix} seeded random active pixels of window 0 of stream 0: "
-                          f"FP64 NDFT + SF + comb (Eq. 6-11), {secs:.1f} s single-threaded")
-    f_avg = statistics.mean(fused_ms)
-    achieved = OPS_PER_TERM * terms_step / (f_avg * 1e-3) / 1e12
-    peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
     line = dict(
         metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
         warmup=args.warmup, ms_per_step=ms_step, higher_is_better=True, scaling="weak",

@@ -358,7 +358,7 @@ int blocked_warp_bytes(const Ctx *c, bool fused, int NW, int *pw_offset) {
 template <int TB, int NW, bool FUSED>
 ddhf_status launch_blocked_t(Ctx *c, int n_slots, float *P, int64_t cap_px, cudaStream_t s,
                              int slot0 = 0) {
-  BlockedArgs A;
+  BlockedArgs A{};
   A.views = c->d_views;
   A.slot0 = slot0;
   A.n_slots = n_slots;

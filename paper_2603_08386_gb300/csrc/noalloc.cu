@@ -73,8 +73,9 @@ __global__ void k_noalloc_heavy(NoAllocScratch *s, const uint32_t *offsets, cons
 template <int TB>
 ddhf_status launch_noalloc(NoAllocScratch *sp, const GridConst &g, float *P, int64_t cap_px,
                            int64_t n_active, int num_sms, cudaStream_t s) {
-  blocked::BlockedArgs A;
+  blocked::BlockedArgs A{};
   A.views = &sp->view;
+  A.slot0 = 0;
   A.n_slots = 1;
   A.npx = n_active;  // light pixels: virtual index over the active list
   A.heavy = sp->heavy;

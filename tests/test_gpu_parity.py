@@ -353,7 +353,7 @@ def test_batch_graph_equals_single_windows():
         masks.fill_(3)
         ddhf.ddhf_detect_batch(cb.h, wins, boxes, cap, nbx, masks, use_graph=use_graph)
         times = ddhf.ddhf_stage_times(cb.h)
-        assert all(t > 0 for t in times)
+        assert all(t > 0 for t in times[:3]) and times[3] == times[4] == 0.0  # fused
         torch.cuda.synchronize()
         for i, (bref, mref) in enumerate(single):
             n = int(nbx[i].item())

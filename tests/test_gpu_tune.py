@@ -32,7 +32,8 @@ def test_autotune_choice_cache_and_parity(tmp_path):
     best, timings = tune.autotune(c, wins, boxes, cap, nb, candidates=cands, cache_path=cache)
     assert best in cands and len(timings) == 3
     assert min(timings.values()) == timings[json.dumps(best, sort_keys=True)]
-    assert ddhf.ddhf_get_tuning(c.h) == best
+    cur = ddhf.ddhf_get_tuning(c.h)
+    assert all(cur[k] == v for k, v in best.items())
     assert os.path.exists(cache)
     again, _ = tune.autotune(c, wins, boxes, cap, nb, candidates=cands[:1], cache_path=cache)
     assert again == best  # served from the cache, no new timing
