@@ -213,9 +213,10 @@ ddhf_status run_detect(Ctx *c, const ddhf_window *wins, int nw, ddhf_box *boxes,
       DDHF_TRY(bin_into(c, w, W.x, W.y, W.t_us, W.p, W.n, W.t0_us, W.window_us, s));
       if (we) DDHF_CUDA_TRY(c, record_event(we[1], s));
       Slot &sl = c->slots[w];
-      DDHF_TRY(launch_spectrum_slot(c, w, c->pbuf, c->npx, s));
+      DDHF_TRY(launch_spectrum_slot(c, w, c->pbuf, c->npx, s, c->pbuf_ld));
       if (we) DDHF_CUDA_TRY(c, record_event(we[2], s));
-      DDHF_TRY(launch_comb(c, c->pbuf, c->npx, sl.log_sf, sl.snr, sl.f0, sl.mask, s, w));
+      DDHF_TRY(launch_comb(c, c->pbuf, c->npx, sl.log_sf, sl.snr, sl.f0, sl.mask, s, w,
+                           c->pbuf_ld));
       if (we) DDHF_CUDA_TRY(c, record_event(we[3], s));
     }
   }
@@ -359,7 +360,8 @@ ddhf_status ddhf_create(int32_t W, int32_t H, const ddhf_grid *grid, const ddhf_
   A(c->box_tmp, 15 * npx);
   A(c->flags, 1);
   A(c->soft_part, 16 * npx + 16);
-  if (grid->n_bins <= 4096) A(c->pbuf, npx * (int64_t)grid->n_bins);
+  c->pbuf_ld = ((int64_t)grid->n_bins + 3) & ~(int64_t)3;  // 16-byte aligned rows
+  if (grid->n_bins <= 4096) A(c->pbuf, npx * c->pbuf_ld);
 #undef A
   if (st == DDHF_OK) {
     cudaMemset(c->qctl, 0, 16 * sizeof(uint32_t));

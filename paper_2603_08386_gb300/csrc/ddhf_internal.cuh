@@ -101,7 +101,8 @@ struct Ctx {
   int32_t *box_tmp = nullptr;    // [npx * 6]
   uint32_t *flags = nullptr;     // [1] DDHF_FLAG_* bits
   float *soft_part = nullptr;    // [16 * npx + 16] soft-comb gradient partials
-  float *pbuf = nullptr;         // [npx * n_bins] spectra of one window (unfused detection)
+  float *pbuf = nullptr;         // [npx * pbuf_ld] spectra of one window (unfused detection)
+  int64_t pbuf_ld = 0;           // row stride of pbuf: n_bins rounded up to 4 floats
   CombConst comb{};
   GridConst gconst{};
   cudaStream_t last_stream = nullptr;
@@ -167,9 +168,11 @@ ddhf_status launch_scan_u32(Ctx *c, const uint32_t *in, uint32_t *out, int64_t n
                             cudaStream_t s);
 // ndft.cu
 ddhf_status launch_spectrum(Ctx *c, int form, float *P, int64_t cap_px, cudaStream_t s);
-ddhf_status launch_spectrum_slot(Ctx *c, int slot, float *P, int64_t cap_px, cudaStream_t s);
+ddhf_status launch_spectrum_slot(Ctx *c, int slot, float *P, int64_t cap_px, cudaStream_t s,
+                                 int64_t ld);
 ddhf_status launch_comb(Ctx *c, const float *P, int64_t cap_px, float *log_sf, float *snr,
-                        int32_t *f0, uint8_t *mask, cudaStream_t s, int slot = 0);
+                        int32_t *f0, uint8_t *mask, cudaStream_t s, int slot = 0,
+                        int64_t ld = 0);
 ddhf_status launch_fused(Ctx *c, int n_slots, bool write_p, float *P, int64_t cap_px,
                          cudaStream_t s);
 void set_bin_attributes();

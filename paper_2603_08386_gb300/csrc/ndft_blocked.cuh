@@ -185,6 +185,7 @@ struct BlockedArgs {
   GridConst g;
   CombConst cc;
   float *P;                  // spectra (write mode), rows in active order of slot 0
+  int64_t ld;                // row stride of P in floats (>= N)
   int64_t cap_px;
   int heavy_min;
   int warp_bytes;            // per-warp shared memory (bytes)
@@ -211,7 +212,7 @@ __device__ __forceinline__ void pixel_spectrum_warp(const BlockedArgs &A, const 
       finalize_tile<TB>(acc, Pw, 0);
       __syncwarp();
       const int j_begin = 32 * b0, j_end = min(g.N, 32 * (b0 + rows_per_pass));
-      for (int j = j_begin + lane; j < j_end; j += 32) A.P[prow * g.N + j] = Pw[j - j_begin];
+      for (int j = j_begin + lane; j < j_end; j += 32) A.P[prow * A.ld + j] = Pw[j - j_begin];
     }
     __syncwarp();
   }
@@ -293,7 +294,7 @@ __global__ void k_blocked(BlockedArgs A) {
           finalize_tile<TB>(acc, Pw, 0);
           __syncwarp();
           const int j_begin = 32 * b0, j_end = min(A.g.N, 32 * (b0 + rows_per_pass));
-          for (int j = j_begin + lane; j < j_end; j += 32) A.P[a * A.g.N + j] = Pw[j - j_begin];
+          for (int j = j_begin + lane; j < j_end; j += 32) A.P[a * A.ld + j] = Pw[j - j_begin];
         }
         __syncwarp();
       }
@@ -347,7 +348,7 @@ int blocked_warp_bytes(const Ctx *c, bool fused, int NW, int *pw_offset) {
   const int partial = 3 * TB * 4 * 32 * 4;
   if (partial > scratch) scratch = partial;
   if (fused) {
-    int cb = CombScratch::bytes(c->grid.n_bins, NW);
+    int cb = comb_scratch_bytes(c->grid.n_bins, NW);
     if (cb > scratch) scratch = cb;
   }
   scratch = (scratch + 15) & ~15;
@@ -357,7 +358,7 @@ int blocked_warp_bytes(const Ctx *c, bool fused, int NW, int *pw_offset) {
 
 template <int TB, int NW, bool FUSED>
 ddhf_status launch_blocked_t(Ctx *c, int n_slots, float *P, int64_t cap_px, cudaStream_t s,
-                             int slot0 = 0) {
+                             int slot0 = 0, int64_t ld = 0) {
   BlockedArgs A{};
   A.views = c->d_views;
   A.slot0 = slot0;
@@ -370,6 +371,7 @@ ddhf_status launch_blocked_t(Ctx *c, int n_slots, float *P, int64_t cap_px, cuda
   A.g = c->gconst;
   A.cc = c->comb;
   A.P = P;
+  A.ld = ld > 0 ? ld : c->gconst.N;
   A.cap_px = cap_px;
   A.heavy_min = c->tuning.heavy_min;
   A.warp_bytes = blocked_warp_bytes<TB>(c, FUSED, NW, &A.pw_offset);
@@ -394,16 +396,22 @@ ddhf_status launch_blocked_t(Ctx *c, int n_slots, float *P, int64_t cap_px, cuda
 
 template <bool FUSED>
 ddhf_status launch_blocked_any(Ctx *c, int n_slots, float *P, int64_t cap_px, cudaStream_t s,
-                               int slot0 = 0) {
+                               int slot0 = 0, int64_t ld = 0) {
   const int nbr = c->gconst.nbr;
   int tb = std::min(8, (nbr + 3) / 4);
   tb = tb <= 2 ? tb : tb <= 4 ? 4 : tb <= 6 ? 6 : 8;
   if (c->tuning.rows_per_lane > 0) tb = c->tuning.rows_per_lane;
-  const int nw = (c->comb.bw + 31) / 32;
+  // fused: the fast comb where it applies, else the generic one with 8 mask words
+  const int variant = comb_variant(c->grid.n_bins, c->comb.bw);
 #define DDHF_TB_CASE(T)                                                           \
   case T:                                                                         \
-    if (!FUSED || nw <= 1) return launch_blocked_t<T, 1, FUSED>(c, n_slots, P, cap_px, s, slot0); \
-    return launch_blocked_t<T, 8, FUSED>(c, n_slots, P, cap_px, s, slot0);
+    if constexpr (!FUSED) {                                                       \
+      return launch_blocked_t<T, 1, false>(c, n_slots, P, cap_px, s, slot0, ld);  \
+    } else {                                                                      \
+      if (variant == 0)                                                           \
+        return launch_blocked_t<T, 0, true>(c, n_slots, P, cap_px, s, slot0, ld); \
+      return launch_blocked_t<T, 8, true>(c, n_slots, P, cap_px, s, slot0, ld);   \
+    }
   switch (tb) {
     DDHF_TB_CASE(1)
     DDHF_TB_CASE(2)

@@ -85,6 +85,7 @@ ddhf_status launch_noalloc(NoAllocScratch *sp, const GridConst &g, float *P, int
   A.g = g;
   A.cc = CombConst{};
   A.P = P;
+  A.ld = g.N;
   A.cap_px = cap_px;
   A.heavy_min = kNoAllocHeavyMin;
   const int stage = blocked::WarpLayout<TB>::kStageF4 * 16;

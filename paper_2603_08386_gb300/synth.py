@@ -369,3 +369,38 @@ def synthetic_spectra(n_px: int, N: int, seed: int) -> np.ndarray:
         elif k == 5 and rng.random() < 0.3:
             P[i] = np.float32(rng.uniform(0.5, 2.0))  # constant row
     return P
+
+
+def clustered_spectra(n_px: int, N: int, seed: int) -> np.ndarray:
+    """Seeded FP32 spectra [n_px, N] whose middle order statistics are crowded:
+    row kinds cycle through (0) zeros below the middle, 40 values spread
+    geometrically over two decades across the middle ranks and large values
+    above (a middle band spanning many binades), (1) values quantised to a coarse step so that hundreds tie, (2) a
+    cluster of 8 distinct values within a few ulps of each other straddling
+    the middle rank, (3) 40 values within 1e-4 relative of the median."""
+    rng = np.random.default_rng(seed)
+    P = rng.exponential(1.0, (n_px, N)).astype(np.float32)
+    for i in range(n_px):
+        k = i % 4
+        row = P[i]
+        if k == 0:
+            perm = rng.permutation(N)
+            n0 = N // 2 - 20
+            big = rng.uniform(50.0, 60.0, N - n0 - 40)
+            mean = big.sum() / N
+            row[perm[:n0]] = 0.0
+            row[perm[n0:n0 + 40]] = (mean * np.geomspace(0.005, 0.5, 40)
+                                     * rng.uniform(0.99, 1.01, 40)).astype(np.float32)
+            row[perm[n0 + 40:]] = big.astype(np.float32)
+        elif k == 1:
+            row[:] = np.round(row * 2.0) / 2.0
+        else:
+            order = np.argsort(row, kind="stable")
+            mid = N // 2 - int(rng.integers(0, 12))
+            m = float(row[order[mid]])
+            width = 8 if k == 2 else 40
+            idx = order[max(0, mid - width // 2):mid + width // 2]
+            rel = 1e-6 if k == 2 else 1e-4
+            row[idx] = (m * (1.0 + rel * rng.random(idx.size))).astype(np.float32)
+    return P
+

@@ -170,11 +170,19 @@ def test_spectrum_capacity_flag():
 
 # ------------------------------------------------------------------ comb
 
-@pytest.mark.parametrize("N,M,d,h_min", [(750, 4, 3, 4), (100, 4, 3, 4), (333, 6, 2, 3),
-                                         (200, 16, 4, 8), (64, 2, 0, 1)])
-def test_comb_bit_exact_on_generated_spectra(N, M, d, h_min):
-    # the comb's input spectra come from the seeded generator; GPU and the
-    # oracle's FP32 restatement must agree bit for bit
+@pytest.mark.parametrize("N,M,d,h_min,kind", [(750, 4, 3, 4, "mixed"), (100, 4, 3, 4, "mixed"),
+                                              (333, 6, 2, 3, "mixed"), (200, 16, 4, 8, "mixed"),
+                                              (64, 2, 0, 1, "mixed"), (1024, 4, 3, 4, "mixed"),
+                                              (1025, 4, 3, 4, "mixed"),
+                                              (750, 4, 3, 4, "clustered"),
+                                              (1024, 4, 3, 4, "clustered"),
+                                              (331, 6, 2, 3, "clustered")])
+def test_comb_bit_exact_on_generated_spectra(N, M, d, h_min, kind):
+    # the comb's input spectra come from the seeded generators; GPU and the
+    # oracle's FP32 restatement must agree bit for bit. "clustered" rows crowd
+    # the middle order statistics (ties, near-equal values, a median among
+    # zeros and tiny values), the cases the fast selection hands to its exact
+    # radix fallback.
     n_px = 600
     W, H = 40, 15  # 600 pixels, one event each -> every pixel active (n_min = 1)
     params = ddhf.default_params(M=M, d=d, h_min=h_min, n_min=1)
@@ -185,7 +193,8 @@ def test_comb_bit_exact_on_generated_spectra(N, M, d, h_min):
     x, y, t, p = ddhf.events_to_device(s)
     c.bin_events(x, y, t, p, 0, 100)
     assert c.n_active() == n_px
-    Pn = synth.synthetic_spectra(n_px, N, seed=N + M)
+    gen = synth.synthetic_spectra if kind == "mixed" else synth.clustered_spectra
+    Pn = gen(n_px, N, seed=N + M)
     out = c.comb_score(torch.from_numpy(Pn).cuda())
     lsf = out["log_sf"].cpu().numpy()
     snr = out["snr"].cpu().numpy()
