@@ -178,8 +178,36 @@ __device__ __forceinline__ int lin_bucket(float v, float scale) {
   return (int)fminf(__fmul_rn(v, scale), 1023.f);
 }
 
+// Smallest float v >= 0 with lin_bucket(v, scale) >= g, for 1 <= g <= 1023;
+// -1 when the search does not settle (the caller then takes an exact path).
+__device__ __forceinline__ float bucket_low(int g, float scale) {
+  float v = __fdiv_rn((float)g, scale);
+  if (!(v > 0.f) || !(v < __int_as_float(0x7f800000))) return -1.f;
+  for (int it = 0; it < 8 && v > 0.f && lin_bucket(__uint_as_float(__float_as_uint(v) - 1u), scale) >= g; ++it)
+    v = __uint_as_float(__float_as_uint(v) - 1u);
+  for (int it = 0; it < 8 && lin_bucket(v, scale) < g; ++it)
+    v = __uint_as_float(__float_as_uint(v) + 1u);
+  const bool ok = lin_bucket(v, scale) >= g &&
+                  (v == 0.f || lin_bucket(__uint_as_float(__float_as_uint(v) - 1u), scale) < g);
+  return ok ? v : -1.f;
+}
+
 __device__ __forceinline__ float snr_of(float nw, float B) {
   return B > 0.f ? __fdiv_rn(nw, B) : (nw > 0.f ? __int_as_float(0x7f800000) : 0.f);
+}
+
+// Natural log of a normal float, ln x = log2(x) ln 2, with the hardware base-2
+// logarithm (PTX lg2.approx, flush-to-zero form; its inputs here are >= 1e-30).
+__device__ __forceinline__ float ln_normal(float x) {
+  float r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return __fmul_rn(r, 0.693147180559945309f);
+}
+
+// N(w) = s / M_valid (Eq. 8); a power-of-two divisor is an exact scaling.
+__device__ __forceinline__ float comb_nw(float s, int mv) {
+  return ((mv & (mv - 1)) == 0) ? __fmul_rn(s, __int_as_float((127 - (__ffs(mv) - 1)) << 23))
+                                : __fdiv_rn(s, (float)mv);
 }
 
 // Eq. 7-11 for the spectrum Pw[0..N) (shared memory) by the calling warp.
@@ -194,7 +222,7 @@ __device__ __forceinline__ CombOut comb_warp_generic(const float *Pw, const Comb
   float slog = 0.f, sum = 0.f;
   for (int j = lane; j < N; j += 32) {
     float v = Pw[j];
-    slog = __fadd_rn(slog, __logf(fmaxf(v, 1e-30f)));
+    slog = __fadd_rn(slog, ln_normal(fmaxf(v, 1e-30f)));
     sum = __fadd_rn(sum, v);
   }
 #pragma unroll
@@ -437,36 +465,43 @@ __device__ __forceinline__ CombOut comb_warp_generic(const float *Pw, const Comb
 // Fast variant for N <= 1024 bins and a median band of at most 32 ranks.
 //
 // Same results as comb_warp_generic, bit for bit, with fewer instructions:
-//  * 2048 linear buckets over [0, 2 mean), two 16-bit counts per word, are
-//    filled in the same pass as the log sum of Eq. 7;
-//  * the buckets holding ranks lo_r and hi_r bound the candidate set; one pass
-//    extracts the candidates and writes the prefix count of bins in lower
-//    buckets (the "below" prefix), so the band is extended downwards to the
-//    first candidate: band position p = full rank cb + p, cb = bins in lower
-//    buckets, and the band covers full ranks [cb, hi_r] (at most 32);
-//  * candidates are sorted in registers as 32-bit keys (value bits relative
-//    to the smallest candidate, above the 10-bit bin index);
-//  * per window centre one float2 record {window maximum, band mask};
-//  * the complement median is picked from the band values by a shuffle.
-// Pixels whose candidates do not fit (more than 64, band wider than 32, or
-// value range above 2^22 ulps) take an exact radix selection of the band
-// [lo_r, hi_r] instead, with the same record layout.
+//  * 1024 linear buckets over [0, 2 mean) are filled in the same pass as the
+//    log sum of Eq. 7 (the Eq. 7 sums take 4-bin groups per lane);
+//  * the buckets holding ranks lo_r and hi_r bound the candidate set, which is
+//    extracted in one pass and sorted in registers as 32-bit keys (value bits
+//    relative to the smallest candidate, above the 10-bit bin index);
+//  * with (T, tj) the value and bin at rank lo_r, a bin lies below the band
+//    exactly when P < T, or P == T at a smaller bin index, so the bins of a
+//    window below the band are counted from the spectrum directly, with no
+//    prefix array;
+//  * one window maximum per window centre and one code byte per bin (band
+//    position, below or above the band), from which a candidate's band mask
+//    and count of bins below the band are gathered; the complement median is
+//    picked from the band values by a shuffle.
+// Pixels whose candidates do not fit (more than 64, or a value range above
+// 2^22 ulps) take an exact radix selection of the band instead.
+// Eq. 8-10 are evaluated in two phases. Every complement median lies between
+// the first and last band values T <= B <= T_hi, so LB = N_max / T_hi (the
+// largest N(w) over candidates) is a lower bound on the best SNR, and a
+// candidate with N(w) / T < LB can neither win nor tie. Phase 1 computes
+// N(w) for all candidates; phase 2 runs the exact median and division only
+// for the candidates that survive this test (or for all of them when more
+// than 64 survive).
 // Scratch layout (bytes from the scratch base, 16-byte aligned):
-//   [0, R)   R = max(8N, 4096): histogram u32[1024] during selection, then the
+//   [0, R)   R = max(5N, 4096): histogram u32[1024] during selection, then the
 //            candidate values u32[64] and indices u16[64] (and the fallback's
-//            radix histogram and keys), then the window records float2[N]
-//   [R, R + 2(N+1))  below prefix u16[N+1]
+//            radix histogram), then the window maxima f32[N] and, from 4N,
+//            one code byte per bin: its band position 0..31, 32 below the
+//            band, 64 above it
+//   [R, R + 128)  surviving candidates u16[64]
 struct CombFast {
-  __host__ __device__ static int rec_bytes(int N) { return 8 * N > 4096 ? 8 * N : 4096; }
-  __host__ __device__ static int preb_off(int N) { return (rec_bytes(N) + 15) & ~15; }
-  __host__ __device__ static int bytes(int N) { return preb_off(N) + ((2 * (N + 1) + 15) & ~15); }
+  __host__ __device__ static int rec_bytes(int N) { return 5 * N > 4096 ? 5 * N : 4096; }
+  __host__ __device__ static int list_off(int N) { return (rec_bytes(N) + 15) & ~15; }
+  __host__ __device__ static int bytes(int N) { return list_off(N) + 128; }
   static constexpr int kMaxN = 1024;
   static constexpr int kMaxBand = 32;
+  static constexpr int kMaxList = 64;
 };
-
-__device__ __forceinline__ int bucket2048(float v, float scale) {
-  return (int)fminf(__fmul_rn(v, scale), 2047.f);
-}
 
 // Bitonic sort (ascending) of 32 keys, one per lane.
 __device__ __forceinline__ uint32_t warp_sort32_u32(uint32_t v) {
@@ -547,13 +582,21 @@ __device__ __forceinline__ int nth_set_bit(uint32_t x, int k) {
   return (k == 0 && (x & 1u)) ? pos : -1;
 }
 
+// Bin j (value v) lies below the band that starts at (T, tj) in the
+// (value, index) order.
+__device__ __forceinline__ bool below_band(float v, int j, float T, int tj) {
+  return v < T || (v == T && j < tj);
+}
+
 __device__ __forceinline__ CombOut comb_warp_fast(const float *Pw, const CombConst &cc,
                                                   unsigned char *scratch) {
   const int lane = threadIdx.x & 31;
   const int N = cc.N;
   const uint32_t lt = lanemask_lt();
   uint32_t *hist = reinterpret_cast<uint32_t *>(scratch);
-  uint16_t *preb = reinterpret_cast<uint16_t *>(scratch + CombFast::preb_off(N));
+  uint16_t *list = reinterpret_cast<uint16_t *>(scratch + CombFast::list_off(N));
+  const float4 *P4 = reinterpret_cast<const float4 *>(Pw);
+  const int ng = (N + 3) >> 2;  // 4-bin groups, the last one possibly partial
   CombOut out;
   out.snr = 0.f;
   out.w = -1;
@@ -561,25 +604,46 @@ __device__ __forceinline__ CombOut comb_warp_fast(const float *Pw, const CombCon
   out.bad = 0;
   bool bad = false;
 
-  // ---- Eq. 7 sums (fixed order: lane-strided, then a butterfly) + histogram
+  // ---- Eq. 7 sums (fixed order: 4-bin groups lane-strided, then a
+  // butterfly) and the histogram
 #pragma unroll
   for (int q = 0; q < 8; ++q)
     reinterpret_cast<uint4 *>(hist)[q * 32 + lane] = make_uint4(0u, 0u, 0u, 0u);
+  // full 4-bin groups, then the (at most 3) tail bins in the lane owning
+  // group N / 4, in bin order
+  const int nfull = N >> 2;
+  const int tail_lane = nfull & 31;
+  const int jt = nfull << 2;
   float sum = 0.f;
-#pragma unroll 4
-  for (int j = lane; j < N; j += 32) sum = __fadd_rn(sum, Pw[j]);
+  for (int q = lane; q < nfull; q += 32) {
+    const float4 v = P4[q];
+    sum = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(sum, v.x), v.y), v.z), v.w);
+  }
+  if (lane == tail_lane)
+    for (int j = jt; j < N; ++j) sum = __fadd_rn(sum, Pw[j]);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) sum = __fadd_rn(sum, __shfl_xor_sync(0xffffffffu, sum, o));
   const float fN = (float)N;
-  const float scale = __fdiv_rn(1024.f, __fdiv_rn(sum, fN));
+  const float scale = __fdiv_rn(512.f, __fdiv_rn(sum, fN));
   __syncwarp();
   float slog = 0.f;
-#pragma unroll 4
-  for (int j = lane; j < N; j += 32) {
-    const float v = Pw[j];
-    slog = __fadd_rn(slog, __logf(fmaxf(v, 1e-30f)));
-    const int g = bucket2048(v, scale);
-    atomicAdd(&hist[g >> 1], 1u << ((g & 1) << 4));
+  for (int q = lane; q < nfull; q += 32) {
+    const float4 v = P4[q];
+    slog = __fadd_rn(slog, ln_normal(fmaxf(v.x, 1e-30f)));
+    slog = __fadd_rn(slog, ln_normal(fmaxf(v.y, 1e-30f)));
+    slog = __fadd_rn(slog, ln_normal(fmaxf(v.z, 1e-30f)));
+    slog = __fadd_rn(slog, ln_normal(fmaxf(v.w, 1e-30f)));
+    atomicAdd(&hist[lin_bucket(v.x, scale)], 1u);
+    atomicAdd(&hist[lin_bucket(v.y, scale)], 1u);
+    atomicAdd(&hist[lin_bucket(v.z, scale)], 1u);
+    atomicAdd(&hist[lin_bucket(v.w, scale)], 1u);
+  }
+  if (lane == tail_lane) {
+    for (int j = jt; j < N; ++j) {
+      const float v = Pw[j];
+      slog = __fadd_rn(slog, ln_normal(fmaxf(v, 1e-30f)));
+      atomicAdd(&hist[lin_bucket(v, scale)], 1u);
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) slog = __fadd_rn(slog, __shfl_xor_sync(0xffffffffu, slog, o));
@@ -587,23 +651,21 @@ __device__ __forceinline__ CombOut comb_warp_fast(const float *Pw, const CombCon
   if (!(out.log_sf <= cc.ln_tau_sf) || cc.w_hi < cc.w_lo) return out;
   __syncwarp();
 
-  // ---- buckets of ranks lo_r and hi_r. Lane l owns words [32 l, 32 l + 32)
-  // (buckets [64 l, 64 l + 64)); both 16-bit halves are summed in one word.
-  const int lo_r = cc.lo_r, hi_r = cc.lo_r + cc.bw - 1;
-  uint32_t acc = 0;
+  // ---- buckets of ranks lo_r and hi_r; lane l owns buckets [32 l, 32 l + 32)
+  const int lo_r = cc.lo_r, bw = cc.bw, hi_r = cc.lo_r + cc.bw - 1;
+  uint32_t lsum = 0;
   {
     const uint4 *h4 = reinterpret_cast<const uint4 *>(hist) + lane * 8;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const uint4 t = h4[(q + lane) & 7];  // rotated: no bank conflicts
-      acc += t.x + t.y + t.z + t.w;
+      lsum += t.x + t.y + t.z + t.w;
     }
   }
-  const uint32_t lsum = (acc & 0xFFFFu) + (acc >> 16);
   uint32_t tot;
   const uint32_t lex = warp_excl_scan<uint32_t>(lsum, tot);
   if (tot != (uint32_t)N) bad = true;
-  int gb[2];
+  int gsel[2];
   uint32_t gbelow[2], gcount[2];
 #pragma unroll
   for (int t = 0; t < 2; ++t) {
@@ -614,59 +676,57 @@ __device__ __forceinline__ CombOut comb_warp_fast(const float *Pw, const CombCon
       bad = true;
     }
     const uint32_t base = __shfl_sync(0xffffffffu, lex, src);
-    const uint32_t wv = hist[src * 32 + lane];
-    const uint32_t c0 = wv & 0xFFFFu, c1 = wv >> 16;
+    const uint32_t h = hist[src * 32 + lane];
     uint32_t t2;
-    const uint32_t ex = warp_excl_scan<uint32_t>(c0 + c1, t2) + base;
-    const bool own = R >= ex && R < ex + c0 + c1;
-    int s2 = __ffs(__ballot_sync(0xffffffffu, own)) - 1;
+    const uint32_t ex = warp_excl_scan<uint32_t>(h, t2) + base;
+    int s2 = __ffs(__ballot_sync(0xffffffffu, R >= ex && R < ex + h)) - 1;
     if (s2 < 0) {
       s2 = 0;
       bad = true;
     }
-    const bool first = R < ex + c0;  // meaningful in lane s2
-    const uint32_t gsel = (uint32_t)(src * 64 + 2 * lane) + (first ? 0u : 1u);
-    const uint32_t gbl = first ? ex : ex + c0;
-    const uint32_t gct = first ? c0 : c1;
-    gb[t] = (int)__shfl_sync(0xffffffffu, gsel, s2);
-    gbelow[t] = __shfl_sync(0xffffffffu, gbl, s2);
-    gcount[t] = __shfl_sync(0xffffffffu, gct, s2);
+    gsel[t] = src * 32 + s2;
+    gbelow[t] = __shfl_sync(0xffffffffu, ex, s2);
+    gcount[t] = __shfl_sync(0xffffffffu, h, s2);
   }
-  int cb = (int)gbelow[0];
+  const int cb = (int)gbelow[0];  // bins in buckets below the candidates
   const int ncand = (int)(gbelow[1] + gcount[1]) - cb;
-  int bwe = hi_r - cb + 1;  // band positions: full ranks [cb, hi_r]
-  bool slow = ncand > 64 || bwe > CombFast::kMaxBand || bad;
+  bool slow = ncand > 64 || bad;
   __syncwarp();
 
-  // ---- candidates (bins of buckets gb[0]..gb[1]) and the below prefix
-  uint32_t *cv = hist;                                         // u32[64]
-  uint16_t *cj = reinterpret_cast<uint16_t *>(scratch + 256);  // u16[64]
-  float bv = 0.f;  // band value at position lane (lane < bwe)
+  // ---- the band: lane p < bw holds the bin at full rank lo_r + p
+  float bv = 0.f;  // its value
   int bj = 0;      // its bin
+  float T = 0.f;   // band start in the (value, index) order: (T, tj)
+  int tj = 0;
   if (!slow) {
-    const int g0 = gb[0];
-    const uint32_t gspan = (uint32_t)(gb[1] - gb[0]);
-    uint32_t run = 0, runb = 0;
-    for (int j0 = 0; j0 <= N; j0 += 32) {
-      const int j = j0 + lane;
-      const float v = j < N ? Pw[j] : 0.f;
-      const int g = bucket2048(v, scale);
-      const bool in = j < N && (uint32_t)(g - g0) <= gspan;
-      const bool below = j < N && g < g0;
-      const uint32_t bi = __ballot_sync(0xffffffffu, in);
-      const uint32_t bb = __ballot_sync(0xffffffffu, below);
-      if (in) {
-        const uint32_t slot = run + __popc(bi & lt);
-        if (slot < 64) {
-          cv[slot] = __float_as_uint(v);
-          cj[slot] = (uint16_t)j;
+    uint32_t *cv = hist;                                         // u32[64]
+    uint16_t *cj = reinterpret_cast<uint16_t *>(scratch + 256);  // u16[64]
+    // candidates are the bins with vlo <= P < vhi, the value bounds of buckets
+    // gsel[0] .. gsel[1] (exact: checked against the bucket function)
+    const float vlo = gsel[0] == 0 ? 0.f : bucket_low(gsel[0], scale);
+    const float vhi = gsel[1] >= 1023 ? __int_as_float(0x7f800000) : bucket_low(gsel[1] + 1, scale);
+    if (vlo < 0.f || vhi < 0.f) slow = true;
+    uint32_t run = 0;
+    for (int q0 = 0; q0 < ng; q0 += 32) {
+      const int q = q0 + lane;
+      const float4 v = q < ng ? P4[q] : make_float4(-1.f, -1.f, -1.f, -1.f);
+      const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int j = 4 * q + u;
+        const bool in = e[u] >= vlo && e[u] < vhi && j < N;
+        const uint32_t bi = __ballot_sync(0xffffffffu, in);
+        if (in) {
+          const uint32_t slot = run + __popc(bi & lt);
+          if (slot < 64) {
+            cv[slot] = __float_as_uint(e[u]);
+            cj[slot] = (uint16_t)j;
+          }
         }
+        run += __popc(bi);
       }
-      if (j <= N) preb[j] = (uint16_t)(runb + __popc(bb & lt));
-      run += __popc(bi);
-      runb += __popc(bb);
     }
-    if ((int)run != ncand || (int)runb != cb) bad = true;
+    if ((int)run != ncand) slow = true;
     __syncwarp();
     const bool in0 = lane < ncand, in1 = lane + 32 < ncand;
     const uint32_t b0 = in0 ? cv[lane] : 0xFFFFFFFFu;
@@ -675,7 +735,7 @@ __device__ __forceinline__ CombOut comb_warp_fast(const float *Pw, const CombCon
     const uint32_t j1v = in1 ? cj[lane + 32] : 0u;
     const uint32_t mn = __reduce_min_sync(0xffffffffu, min(b0, b1));
     const uint32_t mx = __reduce_max_sync(0xffffffffu, max(in0 ? b0 : 0u, in1 ? b1 : 0u));
-    if (mx - mn >= (1u << 22)) {
+    if (slow || mx - mn >= (1u << 22)) {
       slow = true;
     } else {
       uint32_t k0 = in0 ? (((b0 - mn) << 10) | j0v) : 0xFFFFFFFFu;
@@ -685,61 +745,72 @@ __device__ __forceinline__ CombOut comb_warp_fast(const float *Pw, const CombCon
       } else {
         warp_sort64_u32(k0, k1);
       }
-      bv = __uint_as_float((k0 >> 10) + mn);
-      bj = (int)(k0 & 1023u);
+      // sorted element i sits in lane i % 32, register i / 32; band position
+      // p is sorted element p0 + p
+      const int p0 = lo_r - cb;
+      const int i = p0 + lane;
+      const int src = i & 31;
+      const uint32_t kk0 = __shfl_sync(0xffffffffu, k0, src);
+      const uint32_t kk1 = __shfl_sync(0xffffffffu, k1, src);
+      const uint32_t key = i < 32 ? kk0 : kk1;
+      if (lane < bw && i >= ncand) bad = true;
+      bv = __uint_as_float((key >> 10) + mn);
+      bj = (int)(key & 1023u);
+      T = __shfl_sync(0xffffffffu, bv, 0);
+      tj = __shfl_sync(0xffffffffu, bj, 0);
     }
     __syncwarp();
   }
   if (slow) {
-    // exact band [lo_r, hi_r] by radix selection; prefix of bins below it
-    uint32_t *h256 = hist;
-    const uint64_t klo = select_rank_slow(Pw, N, lo_r, h256);
-    const uint64_t khi = select_rank_slow(Pw, N, hi_r, h256);
+    // exact band [lo_r, hi_r] by radix selection
+    const uint64_t klo = select_rank_slow(Pw, N, lo_r, hist);
+    const uint64_t khi = select_rank_slow(Pw, N, hi_r, hist);
     uint64_t key = ~0ull;
-    uint32_t run = 0, runb = 0;
-    for (int j0 = 0; j0 <= N; j0 += 32) {
+    uint32_t run = 0;
+    for (int j0 = 0; j0 < N; j0 += 32) {
       const int j = j0 + lane;
       const uint64_t k = j < N ? bin_key(Pw, j) : ~0ull;
       const bool in = j < N && k >= klo && k <= khi;
-      const bool below = j < N && k < klo;
       const uint32_t bi = __ballot_sync(0xffffffffu, in);
-      const uint32_t bb = __ballot_sync(0xffffffffu, below);
       const uint32_t slot = run + __popc(bi & lt);
-      // one band key per lane: lane `slot` receives it
 #pragma unroll 1
-      for (uint32_t m = bi; m; m &= m - 1) {
+      for (uint32_t m = bi; m; m &= m - 1) {  // lane `slot` receives the key
         const int srcl = __ffs(m) - 1;
         const uint64_t kk = __shfl_sync(0xffffffffu, k, srcl);
         const uint32_t sl = __shfl_sync(0xffffffffu, slot, srcl);
         if ((uint32_t)lane == sl) key = kk;
       }
-      if (j <= N) preb[j] = (uint16_t)(runb + __popc(bb & lt));
       run += __popc(bi);
-      runb += __popc(bb);
     }
-    if ((int)run != cc.bw) bad = true;
+    if ((int)run != bw) bad = true;
     key = warp_sort32_u64(key);
     bv = __uint_as_float((uint32_t)(key >> 16));
     bj = (int)(key & 0xFFFFu);
-    cb = lo_r;
-    bwe = cc.bw;
+    T = __shfl_sync(0xffffffffu, bv, 0);
+    tj = __shfl_sync(0xffffffffu, bj, 0);
     __syncwarp();
   }
 
-  // ---- window records {max of P over [c - d, c + d], band mask of the window}
+  // ---- window maxima: rec[c] = max of P over [c - d, c + d]; bin codes
   const int d = cc.d;
-  float2 *rec = reinterpret_cast<float2 *>(scratch);
+  float *rec = reinterpret_cast<float *>(scratch);
+  uint8_t *code = scratch + 4 * N;
   if (d == 3) {
-    // centre pairs (2q, 2q + 1): bins 2q - 4 .. 2q + 5 by five 8-byte loads
+    // centre pairs (2q, 2q + 1): bins 2q - 3 .. 2q + 4 by five 8-byte loads
     const float2 *P2 = reinterpret_cast<const float2 *>(Pw);
     const int npair = (N + 1) >> 1;
     for (int q = lane; q < npair; q += 32) {
       float2 a[5];
+      if (q >= 2 && 2 * q + 5 < N) {
 #pragma unroll
-      for (int u = 0; u < 5; ++u) {
-        const int pi = q - 2 + u;  // pair index of bins 2 pi, 2 pi + 1
-        if (pi >= 0 && 2 * pi + 1 < N) a[u] = P2[pi];
-        else a[u] = make_float2(pi >= 0 && 2 * pi < N ? Pw[2 * pi] : 0.f, 0.f);
+        for (int u = 0; u < 5; ++u) a[u] = P2[q - 2 + u];
+      } else {
+#pragma unroll
+        for (int u = 0; u < 5; ++u) {
+          const int pi = q - 2 + u;  // pair index of bins 2 pi, 2 pi + 1
+          a[u].x = (pi >= 0 && 2 * pi < N) ? Pw[2 * pi] : 0.f;
+          a[u].y = (pi >= 0 && 2 * pi + 1 < N) ? Pw[2 * pi + 1] : 0.f;
+        }
       }
       // bins: a[0] = (2q-4, 2q-3), a[1] = (2q-2, 2q-1), a[2] = (2q, 2q+1),
       //       a[3] = (2q+2, 2q+3), a[4] = (2q+4, 2q+5)
@@ -747,10 +818,14 @@ __device__ __forceinline__ CombOut comb_warp_fast(const float *Pw, const CombCon
                               fmaxf(a[3].x, a[3].y));  // 2q-2 .. 2q+3
       const float w0 = fmaxf(mid, a[0].y);             // 2q-3 .. 2q+3
       const float w1 = fmaxf(mid, a[4].x);             // 2q-2 .. 2q+4
+      const uint32_t k0 = below_band(a[2].x, 2 * q, T, tj) ? 32u : 64u;
+      const uint32_t k1 = below_band(a[2].y, 2 * q + 1, T, tj) ? 32u : 64u;
       if (2 * q + 1 < N) {
-        reinterpret_cast<float4 *>(rec)[q] = make_float4(w0, 0.f, w1, 0.f);
+        reinterpret_cast<float2 *>(rec)[q] = make_float2(w0, w1);
+        reinterpret_cast<uint16_t *>(code)[q] = (uint16_t)(k0 | (k1 << 8));
       } else {
-        rec[2 * q] = make_float2(w0, 0.f);
+        rec[2 * q] = w0;
+        code[2 * q] = (uint8_t)k0;
       }
     }
   } else {
@@ -760,51 +835,144 @@ __device__ __forceinline__ CombOut comb_warp_fast(const float *Pw, const CombCon
         mx = Pw[c - d];
         for (int i = 1; i <= 2 * d; ++i) mx = fmaxf(mx, Pw[c - d + i]);
       }
-      rec[c] = make_float2(mx, 0.f);
+      rec[c] = mx;
+      code[c] = below_band(Pw[c], c, T, tj) ? 32u : 64u;
     }
   }
   __syncwarp();
-  if (lane < bwe) {
-    uint32_t *recw = reinterpret_cast<uint32_t *>(rec);
-    const int c_lo = max(0, bj - d), c_hi = min(N - 1, bj + d);
-    for (int c = c_lo; c <= c_hi; ++c) atomicOr(&recw[2 * c + 1], 1u << lane);
-  }
+  if (lane < bw) code[bj] = (uint8_t)lane;
   __syncwarp();
 
-  // ---- Eq. 8-10 for every candidate fundamental, one per lane
-  const uint32_t outside = bwe >= 32 ? 0u : (0xFFFFFFFFu << bwe);
+  // ---- Eq. 8-10, phase 1: N(w) of every candidate and the largest one.
+  // When every candidate has M_valid = M and a non-empty complement (always
+  // for h_min >= M and N > M(2d+1)), N(w) is a plain sum over M windows.
+  const int L = N - 1 - d;
+  const int M = cc.M;
+  const int n_cand = cc.w_hi - cc.w_lo + 1;
+  const bool uniform = M * cc.w_hi <= L && N > M * (2 * d + 1);
+  float maxnw = 0.f;
+  if (uniform) {
+    for (int i0 = 0; i0 < n_cand; i0 += 32) {
+      const int w = cc.w_lo + i0 + lane;
+      if (i0 + lane < n_cand) {
+        float s = 0.f;
+        int c0 = 0;
+#pragma unroll 4
+        for (int m = 0; m < M; ++m) {
+          c0 += w;
+          s = __fadd_rn(s, rec[c0]);
+        }
+        maxnw = fmaxf(maxnw, s);  // same order as N(w): a common scaling
+      }
+    }
+    maxnw = comb_nw(maxnw, M);
+  } else {
+    for (int i0 = 0; i0 < n_cand; i0 += 32) {
+      const int w = cc.w_lo + i0 + lane;
+      if (i0 + lane < n_cand) {
+        int mv = M;
+        while (mv * w > L) --mv;
+        const int h = w >= 2 * d + 1 ? mv * (2 * d + 1) : (mv - 1) * w + 2 * d + 1;
+        float s = 0.f;
+        int c0 = 0;
+        for (int m = 1; m <= mv; ++m) {
+          c0 += w;
+          s = __fadd_rn(s, rec[c0]);
+        }
+        if (N - h > 0) maxnw = fmaxf(maxnw, comb_nw(s, mv));
+      }
+    }
+  }
+  maxnw = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(maxnw)));  // >= 0
+  const float Thi = __shfl_sync(0xffffffffu, bv, bw - 1);
+  const float LB = snr_of(maxnw, Thi);
+  // keep w when N(w) >= thr; thr <= LB T (1 - 2^-20) (1 + 2^-23), so a
+  // dropped candidate has N(w) / T < LB (1 - 2^-21) and SNR(w) < LB
+  // (LB and LB T normal and finite, so that the relative rounding bounds hold)
+  const float lbt = __fmul_rn(LB, T);
+  const bool prune = T > 0.f && LB >= 0x1p-126f && LB < __int_as_float(0x7f800000) &&
+                     lbt >= 0x1p-100f && lbt < __int_as_float(0x7f800000);
+  const float thr = prune ? __fmul_rn(lbt, 1.0f - 0x1p-20f) : 0.f;
+
+  // ---- surviving candidates, in increasing w
+  int n_items = n_cand;
+  bool use_list = false;
+  if (prune) {
+    uint32_t run = 0;
+    for (int i0 = 0; i0 < n_cand; i0 += 32) {
+      const int w = cc.w_lo + i0 + lane;
+      bool keep = false;
+      if (i0 + lane < n_cand) {
+        int mv = M;
+        if (!uniform)
+          while (mv * w > L) --mv;
+        float s = 0.f;
+        int c0 = 0;
+#pragma unroll 4
+        for (int m = 1; m <= mv; ++m) {
+          c0 += w;
+          s = __fadd_rn(s, rec[c0]);
+        }
+        keep = comb_nw(s, mv) >= thr;
+      }
+      const uint32_t b = __ballot_sync(0xffffffffu, keep);
+      const uint32_t slot = run + __popc(b & lt);
+      if (keep && slot < (uint32_t)CombFast::kMaxList) list[slot] = (uint16_t)w;
+      run += __popc(b);
+    }
+    if (run <= (uint32_t)CombFast::kMaxList) {
+      use_list = true;
+      n_items = (int)run;
+    }
+    __syncwarp();
+  }
+
+  // ---- phase 2: exact SNR of the surviving candidates, one per lane: the
+  // band mask of H(w) and its bins below the band from the bin codes
+  const uint32_t outside = bw >= 32 ? 0u : (0xFFFFFFFFu << bw);
   float best = 0.f;
   int bestw = -1;
-  const int L = N - 1 - d;
-  for (int w0 = cc.w_lo; w0 <= cc.w_hi; w0 += 32) {
-    const int w = w0 + lane;
-    const bool ok = w <= cc.w_hi;
+  for (int i0 = 0; i0 < n_items; i0 += 32) {
+    const int nk = min(32, n_items - i0);
+    const int wl = lane < nk ? (use_list ? (int)list[i0 + lane] : cc.w_lo + i0 + lane) : 1;
+    int my_below = 0;
+    uint32_t my_mask = 0u;
+    if (lane < nk) {
+      int mvk = M;
+      while (mvk * wl > L) --mvk;
+      int j_lo = wl - d, j_hi = mvk * wl + d;  // overlapping windows: one range
+      const int nwin = wl >= 2 * d + 1 ? mvk : 1;
+      for (int m = 1; m <= nwin; ++m) {
+        if (wl >= 2 * d + 1) {
+          j_lo = m * wl - d;
+          j_hi = m * wl + d;
+        }
+#pragma unroll 7
+        for (int j = j_lo; j <= j_hi; ++j) {
+          const uint32_t k = code[j];
+          my_mask |= __funnelshift_lc(0u, 1u, k);  // 1 << k, 0 for k >= 32
+          my_below += (int)((k >> 5) & 1u);
+        }
+      }
+    }
+    const bool ok = lane < nk;
+    const int w = wl;
     int pos0 = 0, pos1 = 0, c = 0, mv = 1;
     float s = 0.f;
     if (ok) {
-      mv = cc.M;
+      mv = M;
       while (mv * w > L) --mv;
-      uint32_t mask = outside;
-      int below = 0, cc0 = 0;
+      int c0 = 0;
 #pragma unroll 4
       for (int m = 1; m <= mv; ++m) {
-        cc0 += w;
-        const float2 r = rec[cc0];
-        s = __fadd_rn(s, r.x);
-        mask |= __float_as_uint(r.y);
-        below += (int)preb[cc0 + d + 1] - (int)preb[cc0 - d];
+        c0 += w;
+        s = __fadd_rn(s, rec[c0]);
       }
-      int h;
-      if (w >= 2 * d + 1) {
-        h = mv * (2 * d + 1);
-      } else {  // overlapping windows: their union is one contiguous range
-        h = (mv - 1) * w + 2 * d + 1;
-        below = (int)preb[mv * w + d + 1] - (int)preb[w - d];
-      }
+      const int h = w >= 2 * d + 1 ? mv * (2 * d + 1) : (mv - 1) * w + 2 * d + 1;
       c = N - h;
       if (c > 0) {
-        const int t = (c - 1) / 2 - (cb - below);
-        const uint32_t freeb = ~mask;
+        const int t = (c - 1) / 2 - (lo_r - my_below);
+        const uint32_t freeb = ~(my_mask | outside);
         pos0 = t >= 0 ? nth_set_bit(freeb, t) : -1;
         if (pos0 < 0) {
           pos0 = 0;
@@ -821,11 +989,9 @@ __device__ __forceinline__ CombOut comb_warp_fast(const float *Pw, const CombCon
     const float v0 = __shfl_sync(0xffffffffu, bv, pos0);
     const float v1 = __shfl_sync(0xffffffffu, bv, pos1);
     if (ok && c > 0) {
-      const float nw = ((mv & (mv - 1)) == 0) ? __fmul_rn(s, 1.0f / (float)mv)
-                                              : __fdiv_rn(s, (float)mv);
       const float B = (c & 1) ? v0 : __fmul_rn(__fadd_rn(v0, v1), 0.5f);
-      const float snr = snr_of(nw, B);
-      if (bestw < 0 || snr > best) {
+      const float snr = snr_of(comb_nw(s, mv), B);
+      if (bestw < 0 || snr > best || (snr == best && w < bestw)) {
         best = snr;
         bestw = w;
       }
@@ -850,9 +1016,10 @@ __device__ __forceinline__ CombOut comb_warp_fast(const float *Pw, const CombCon
 
 // Which comb variant a context uses: 0 = fast (N <= 1024, band <= 32),
 // otherwise the generic one with NW mask words per centre.
-__host__ __device__ inline int comb_variant(int N, int bw) {
-  if (N <= CombFast::kMaxN && bw <= CombFast::kMaxBand) return 0;
-  return bw <= 32 ? 1 : 8;
+__host__ __device__ inline int comb_variant(const CombConst &cc) {
+  if (cc.N <= CombFast::kMaxN && cc.bw <= CombFast::kMaxBand && cc.M * (2 * cc.d + 1) <= 32)
+    return 0;
+  return cc.bw <= 32 ? 1 : 8;
 }
 
 __host__ __device__ inline int comb_scratch_bytes(int N, int variant) {

@@ -402,7 +402,7 @@ ddhf_status launch_blocked_any(Ctx *c, int n_slots, float *P, int64_t cap_px, cu
   tb = tb <= 2 ? tb : tb <= 4 ? 4 : tb <= 6 ? 6 : 8;
   if (c->tuning.rows_per_lane > 0) tb = c->tuning.rows_per_lane;
   // fused: the fast comb where it applies, else the generic one with 8 mask words
-  const int variant = comb_variant(c->grid.n_bins, c->comb.bw);
+  const int variant = comb_variant(c->comb);
 #define DDHF_TB_CASE(T)                                                           \
   case T:                                                                         \
     if constexpr (!FUSED) {                                                       \
