@@ -796,36 +796,45 @@ __device__ __forceinline__ CombOut comb_warp_fast(const float *Pw, const CombCon
   float *rec = reinterpret_cast<float *>(scratch);
   uint8_t *code = scratch + 4 * N;
   if (d == 3) {
-    // centre pairs (2q, 2q + 1): bins 2q - 3 .. 2q + 4 by five 8-byte loads
-    const float2 *P2 = reinterpret_cast<const float2 *>(Pw);
-    const int npair = (N + 1) >> 1;
-    for (int q = lane; q < npair; q += 32) {
-      float2 a[5];
-      if (q >= 2 && 2 * q + 5 < N) {
-#pragma unroll
-        for (int u = 0; u < 5; ++u) a[u] = P2[q - 2 + u];
+    // centre quads 4q .. 4q + 3: bins 4q - 4 .. 4q + 7 by three 16-byte loads
+    const int nq4 = N >> 2;  // quads whose bins 4q .. 4q + 3 are all < N
+    for (int q = lane; q < ng; q += 32) {
+      float b[12];  // b[i] = P[4q - 4 + i]
+      if (q >= 1 && q + 1 < nq4) {
+        const float4 x = P4[q - 1], y = P4[q], z = P4[q + 1];
+        b[0] = x.x; b[1] = x.y; b[2] = x.z; b[3] = x.w;
+        b[4] = y.x; b[5] = y.y; b[6] = y.z; b[7] = y.w;
+        b[8] = z.x; b[9] = z.y; b[10] = z.z; b[11] = z.w;
       } else {
 #pragma unroll
-        for (int u = 0; u < 5; ++u) {
-          const int pi = q - 2 + u;  // pair index of bins 2 pi, 2 pi + 1
-          a[u].x = (pi >= 0 && 2 * pi < N) ? Pw[2 * pi] : 0.f;
-          a[u].y = (pi >= 0 && 2 * pi + 1 < N) ? Pw[2 * pi + 1] : 0.f;
+        for (int i = 0; i < 12; ++i) {
+          const int j = 4 * q - 4 + i;
+          b[i] = (j >= 0 && j < N) ? Pw[j] : 0.f;
         }
       }
-      // bins: a[0] = (2q-4, 2q-3), a[1] = (2q-2, 2q-1), a[2] = (2q, 2q+1),
-      //       a[3] = (2q+2, 2q+3), a[4] = (2q+4, 2q+5)
-      const float mid = fmaxf(fmaxf(fmaxf(a[1].x, a[1].y), fmaxf(a[2].x, a[2].y)),
-                              fmaxf(a[3].x, a[3].y));  // 2q-2 .. 2q+3
-      const float w0 = fmaxf(mid, a[0].y);             // 2q-3 .. 2q+3
-      const float w1 = fmaxf(mid, a[4].x);             // 2q-2 .. 2q+4
-      const uint32_t k0 = below_band(a[2].x, 2 * q, T, tj) ? 32u : 64u;
-      const uint32_t k1 = below_band(a[2].y, 2 * q + 1, T, tj) ? 32u : 64u;
-      if (2 * q + 1 < N) {
-        reinterpret_cast<float2 *>(rec)[q] = make_float2(w0, w1);
-        reinterpret_cast<uint16_t *>(code)[q] = (uint16_t)(k0 | (k1 << 8));
-      } else {
-        rec[2 * q] = w0;
-        code[2 * q] = (uint8_t)k0;
+      const float mid = fmaxf(fmaxf(b[4], b[5]), fmaxf(b[6], b[7]));  // 4q .. 4q+3
+      const float l1 = fmaxf(b[2], b[3]), r1 = fmaxf(b[8], b[9]);
+      const float w0 = fmaxf(mid, fmaxf(b[1], l1));   // 4q-3 .. 4q+3
+      const float w1 = fmaxf(mid, fmaxf(l1, b[8]));   // 4q-2 .. 4q+4
+      const float w2 = fmaxf(mid, fmaxf(b[3], r1));   // 4q-1 .. 4q+5
+      const float w3 = fmaxf(mid, fmaxf(r1, b[10]));  // 4q   .. 4q+6
+      const int j0 = 4 * q;
+      const uint32_t k0 = below_band(b[4], j0, T, tj) ? 32u : 64u;
+      const uint32_t k1 = below_band(b[5], j0 + 1, T, tj) ? 32u : 64u;
+      const uint32_t k2 = below_band(b[6], j0 + 2, T, tj) ? 32u : 64u;
+      const uint32_t k3 = below_band(b[7], j0 + 3, T, tj) ? 32u : 64u;
+      if (q < nq4) {
+        reinterpret_cast<float4 *>(rec)[q] = make_float4(w0, w1, w2, w3);
+        reinterpret_cast<uint32_t *>(code)[q] = k0 | (k1 << 8) | (k2 << 16) | (k3 << 24);
+      } else {  // the partial last quad
+        const float wv[4] = {w0, w1, w2, w3};
+        const uint32_t kv[4] = {k0, k1, k2, k3};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (j0 + u < N) {
+            rec[j0 + u] = wv[u];
+            code[j0 + u] = (uint8_t)kv[u];
+          }
       }
     }
   } else {
@@ -850,8 +859,35 @@ __device__ __forceinline__ CombOut comb_warp_fast(const float *Pw, const CombCon
   const int M = cc.M;
   const int n_cand = cc.w_hi - cc.w_lo + 1;
   const bool uniform = M * cc.w_hi <= L && N > M * (2 * d + 1);
+  // In the uniform case with at most 256 candidates, lane l keeps the window
+  // sums of its candidates l + 32 k in registers for the survivor pass.
+  constexpr int kSlots = 8;
+  const bool in_regs = uniform && n_cand <= 32 * kSlots;
+  float sv[kSlots];
   float maxnw = 0.f;
-  if (uniform) {
+  if (in_regs) {
+    float maxs = 0.f;
+#pragma unroll
+    for (int k = 0; k < kSlots; ++k) {
+      sv[k] = 0.f;
+      if (32 * k < n_cand) {
+        const int i = 32 * k + lane;
+        const int w = cc.w_lo + i;
+        if (i < n_cand) {
+          float s = 0.f;
+          int c0 = 0;
+#pragma unroll 4
+          for (int m = 0; m < M; ++m) {
+            c0 += w;
+            s = __fadd_rn(s, rec[c0]);
+          }
+          sv[k] = s;
+          maxs = fmaxf(maxs, s);  // same order as N(w): a common scaling
+        }
+      }
+    }
+    maxnw = comb_nw(maxs, M);
+  } else if (uniform) {
     for (int i0 = 0; i0 < n_cand; i0 += 32) {
       const int w = cc.w_lo + i0 + lane;
       if (i0 + lane < n_cand) {
@@ -862,7 +898,7 @@ __device__ __forceinline__ CombOut comb_warp_fast(const float *Pw, const CombCon
           c0 += w;
           s = __fadd_rn(s, rec[c0]);
         }
-        maxnw = fmaxf(maxnw, s);  // same order as N(w): a common scaling
+        maxnw = fmaxf(maxnw, s);
       }
     }
     maxnw = comb_nw(maxnw, M);
@@ -899,26 +935,40 @@ __device__ __forceinline__ CombOut comb_warp_fast(const float *Pw, const CombCon
   bool use_list = false;
   if (prune) {
     uint32_t run = 0;
-    for (int i0 = 0; i0 < n_cand; i0 += 32) {
-      const int w = cc.w_lo + i0 + lane;
-      bool keep = false;
-      if (i0 + lane < n_cand) {
-        int mv = M;
-        if (!uniform)
-          while (mv * w > L) --mv;
-        float s = 0.f;
-        int c0 = 0;
-#pragma unroll 4
-        for (int m = 1; m <= mv; ++m) {
-          c0 += w;
-          s = __fadd_rn(s, rec[c0]);
+    if (in_regs) {
+#pragma unroll
+      for (int k = 0; k < kSlots; ++k) {
+        if (32 * k < n_cand) {
+          const int i = 32 * k + lane;
+          const bool keep = i < n_cand && comb_nw(sv[k], M) >= thr;
+          const uint32_t b = __ballot_sync(0xffffffffu, keep);
+          const uint32_t slot = run + __popc(b & lt);
+          if (keep && slot < (uint32_t)CombFast::kMaxList) list[slot] = (uint16_t)(cc.w_lo + i);
+          run += __popc(b);
         }
-        keep = comb_nw(s, mv) >= thr;
       }
-      const uint32_t b = __ballot_sync(0xffffffffu, keep);
-      const uint32_t slot = run + __popc(b & lt);
-      if (keep && slot < (uint32_t)CombFast::kMaxList) list[slot] = (uint16_t)w;
-      run += __popc(b);
+    } else {
+      for (int i0 = 0; i0 < n_cand; i0 += 32) {
+        const int w = cc.w_lo + i0 + lane;
+        bool keep = false;
+        if (i0 + lane < n_cand) {
+          int mv = M;
+          if (!uniform)
+            while (mv * w > L) --mv;
+          float s = 0.f;
+          int c0 = 0;
+#pragma unroll 4
+          for (int m = 1; m <= mv; ++m) {
+            c0 += w;
+            s = __fadd_rn(s, rec[c0]);
+          }
+          keep = comb_nw(s, mv) >= thr;
+        }
+        const uint32_t b = __ballot_sync(0xffffffffu, keep);
+        const uint32_t slot = run + __popc(b & lt);
+        if (keep && slot < (uint32_t)CombFast::kMaxList) list[slot] = (uint16_t)w;
+        run += __popc(b);
+      }
     }
     if (run <= (uint32_t)CombFast::kMaxList) {
       use_list = true;
