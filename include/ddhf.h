@@ -155,6 +155,9 @@ typedef struct {
  *                   per window, a spectrum kernel writes a context-owned
  *                   buffer that a separate comb kernel reads (more warps per
  *                   SM for the latency-bound comb). Same results either way.
+ * Defaults: heavy_min 1024, 4 warps per block, blocks_per_sm 0, rows_per_lane
+ * 0, fuse 0 (the unfused path needs the context's spectrum buffer, present
+ * when n_bins <= 4096; larger grids always run fused).
  * Different tunings give spectra that agree within the FP32 rounding of the
  * summation order; each tuning is deterministic. */
 typedef struct {

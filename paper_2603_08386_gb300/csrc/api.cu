@@ -112,6 +112,7 @@ void derive_constants(Ctx *c) {
   k.denom = (uint64_t)g.denom;
   k.barrett = ~0ull / (uint64_t)g.denom;
   k.da_mod = (uint64_t)g.da % (uint64_t)g.denom;
+  k.da16_mod = ((uint64_t)g.da * 16ull) % (uint64_t)g.denom;
   k.da32_mod = ((uint64_t)g.da * 32ull) % (uint64_t)g.denom;
   k.N = g.n_bins;
   k.nbr = (g.n_bins + 31) / 32;
@@ -299,7 +300,7 @@ ddhf_status ddhf_create(int32_t W, int32_t H, const ddhf_grid *grid, const ddhf_
   c->params = *params;
   c->max_events = max_events;
   c->max_windows = max_windows;
-  c->tuning = ddhf_tuning{1024, 4, 0, 0, 1, 0};
+  c->tuning = ddhf_tuning{1024, 4, 0, 0, 0, 0};
   cudaError_t e = cudaGetDevice(&c->device);
   if (e == cudaSuccess)
     e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);

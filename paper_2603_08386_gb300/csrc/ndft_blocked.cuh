@@ -52,64 +52,79 @@ struct WarpLayout {
   static constexpr int kStageF4 = kA + kGenChunk * ALayout<TB>::kEvent;
 };
 
-// Generate the A and B factors of events [0, ne) of one chunk (ev points at
-// the chunk's first event). Lanes 0-15 write B rows, lanes 16-31 A rows.
+// Generate the A and B factors of events [0, ne) of one chunk (evp points at
+// the chunk's first event). Two lanes per event run the same code: lane e
+// (half 0) writes B columns r = 0..15 and A rows 0..2TB-1, lane e + 16
+// (half 1) B columns 16..31 and A rows 2TB..4TB-1, each from exact seeds
+// (residues of its first column / row) stepped by the exact unit phasors
+// u = e^{-2 pi i da tau / D} (columns) and u^32 (rows).
+// arow_mod[h]: (a of the first A row of half h) mod D.
 template <int TB>
 __device__ __forceinline__ void gen_chunk(const uint32_t *__restrict__ evp, int ne,
-                                          const GridConst &g, uint64_t arow_mod, float4 *stage) {
+                                          const GridConst &g, const uint64_t (&arow_mod)[2],
+                                          float4 *stage) {
   const int lane = threadIdx.x & 31;
-  const int e = lane & 15;
+  const int e = lane & 15, half = lane >> 4;
   if (e >= ne) return;
   const uint32_t w = evp[e];
   const uint64_t tau = w & 0x7fffffffu;
-  if (lane < 16) {
-    const uint64_t r = mod_barrett(g.da_mod * tau, g.denom, g.barrett);
-    const float2 u = phasor_of_residue(r, g.two_over_denom);
-    float2 z = make_float2(1.f, 0.f);
-    float4 *dst = stage + WarpLayout<TB>::kB + e * kBEvent;
+  const uint64_t rz = mod_barrett((half ? g.da16_mod : 0ull) * tau, g.denom, g.barrett);
+  const uint64_t ru = mod_barrett(g.da_mod * tau, g.denom, g.barrett);
+  const uint64_t rs = mod_barrett(arow_mod[half] * tau, g.denom, g.barrett);
+  const uint64_t rv = mod_barrett(g.da32_mod * tau, g.denom, g.barrett);
+  float2 z = phasor_of_residue(rz, g.two_over_denom);
+  const float2 u = phasor_of_residue(ru, g.two_over_denom);
+  float2 s = phasor_of_residue(rs, g.two_over_denom);
+  const float2 v = phasor_of_residue(rv, g.two_over_denom);
+  if (!half) z = make_float2(1.f, 0.f);
+  if (w & kSignBit) {
+    s.x = -s.x;
+    s.y = -s.y;
+  }
+  float4 *dstb = stage + WarpLayout<TB>::kB + e * kBEvent + half * 4 * 3;
 #pragma unroll
-    for (int rg = 0; rg < 8; ++rg) {
-      float br[4], bi[4];
+  for (int rg = 0; rg < 4; ++rg) {
+    float br[4], bi[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        br[q] = z.x;
-        bi[q] = z.y;
-        z = cmul(z, u);
-      }
-      dst[rg * 3 + 0] = make_float4(br[0], br[1], br[2], br[3]);
-      dst[rg * 3 + 1] = make_float4(bi[0], bi[1], bi[2], bi[3]);
-      dst[rg * 3 + 2] = make_float4(__fadd_rn(br[0], bi[0]), __fadd_rn(br[1], bi[1]),
-                                    __fadd_rn(br[2], bi[2]), __fadd_rn(br[3], bi[3]));
+    for (int q = 0; q < 4; ++q) {
+      br[q] = z.x;
+      bi[q] = z.y;
+      if (rg < 3 || q < 3) z = cmul(z, u);
     }
-  } else {
-    const uint64_t r0 = mod_barrett(arow_mod * tau, g.denom, g.barrett);
-    const uint64_t rs = mod_barrett(g.da32_mod * tau, g.denom, g.barrett);
-    float2 s = phasor_of_residue(r0, g.two_over_denom);
-    if (w & kSignBit) {
-      s.x = -s.x;
-      s.y = -s.y;
-    }
-    const float2 v = phasor_of_residue(rs, g.two_over_denom);
-    float4 *dst = stage + WarpLayout<TB>::kA + e * ALayout<TB>::kEvent;
+    dstb[rg * 3 + 0] = make_float4(br[0], br[1], br[2], br[3]);
+    dstb[rg * 3 + 1] = make_float4(bi[0], bi[1], bi[2], bi[3]);
+    dstb[rg * 3 + 2] = make_float4(__fadd_rn(br[0], bi[0]), __fadd_rn(br[1], bi[1]),
+                                   __fadd_rn(br[2], bi[2]), __fadd_rn(br[3], bi[3]));
+  }
+  float4 *dsta = stage + WarpLayout<TB>::kA + e * ALayout<TB>::kEvent +
+                 half * 2 * ALayout<TB>::kGroup;
 #pragma unroll
-    for (int bg = 0; bg < 4; ++bg) {
+  for (int bg = 0; bg < 2; ++bg) {
 #pragma unroll
-      for (int i = 0; i < TB; ++i) {
-        dst[bg * ALayout<TB>::kGroup + i] = make_float4(s.x, s.y, __fadd_rn(s.x, s.y), 0.f);
-        s = cmul(s, v);
-      }
+    for (int i = 0; i < TB; ++i) {
+      dsta[bg * ALayout<TB>::kGroup + i] = make_float4(s.x, s.y, __fadd_rn(s.x, s.y), 0.f);
+      if (bg < 1 || i < TB - 1) s = cmul(s, v);
     }
   }
 }
 
+// Accumulators of a lane's TB x 4 tile, bins (q, q + 1) of a row packed in a
+// float2 so that one paired FMA (FFMA2, each element rounded on its own)
+// serves two bins.
 template <int TB>
 struct Acc {
-  float t1[TB][4], t2[TB][4], t3[TB][4];
+  float2 t1[TB][2], t2[TB][2], t3[TB][2];
   __device__ __forceinline__ void zero() {
 #pragma unroll
     for (int i = 0; i < TB; ++i)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) t1[i][q] = t2[i][q] = t3[i][q] = 0.f;
+      for (int h = 0; h < 2; ++h) t1[i][h] = t2[i][h] = t3[i][h] = make_float2(0.f, 0.f);
+  }
+  __device__ __forceinline__ float &at(float2 (&t)[TB][2], int i, int q) {
+    return (q & 1) ? t[i][q >> 1].y : t[i][q >> 1].x;
+  }
+  __device__ __forceinline__ float get(const float2 (&t)[TB][2], int i, int q) const {
+    return (q & 1) ? t[i][q >> 1].y : t[i][q >> 1].x;
   }
 };
 
@@ -123,17 +138,19 @@ __device__ __forceinline__ void gemm_chunk(int ne, const float4 *stage, Acc<TB> 
     const float4 br = sb[e * kBEvent + 0];
     const float4 bi = sb[e * kBEvent + 1];
     const float4 bs = sb[e * kBEvent + 2];
-    const float brr[4] = {br.x, br.y, br.z, br.w};
-    const float bii[4] = {bi.x, bi.y, bi.z, bi.w};
-    const float bss[4] = {bs.x, bs.y, bs.z, bs.w};
+    const float2 brr[2] = {make_float2(br.x, br.y), make_float2(br.z, br.w)};
+    const float2 bii[2] = {make_float2(bi.x, bi.y), make_float2(bi.z, bi.w)};
+    const float2 bss[2] = {make_float2(bs.x, bs.y), make_float2(bs.z, bs.w)};
 #pragma unroll
     for (int i = 0; i < TB; ++i) {
       const float4 a = sa[e * ALayout<TB>::kEvent + i];
+      const float2 ax = make_float2(a.x, a.x), ay = make_float2(a.y, a.y);
+      const float2 az = make_float2(a.z, a.z);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        acc.t1[i][q] = __fmaf_rn(a.x, brr[q], acc.t1[i][q]);
-        acc.t2[i][q] = __fmaf_rn(a.y, bii[q], acc.t2[i][q]);
-        acc.t3[i][q] = __fmaf_rn(a.z, bss[q], acc.t3[i][q]);
+      for (int h = 0; h < 2; ++h) {
+        acc.t1[i][h] = __ffma2_rn(ax, brr[h], acc.t1[i][h]);
+        acc.t2[i][h] = __ffma2_rn(ay, bii[h], acc.t2[i][h]);
+        acc.t3[i][h] = __ffma2_rn(az, bss[h], acc.t3[i][h]);
       }
     }
   }
@@ -143,7 +160,8 @@ __device__ __forceinline__ void gemm_chunk(int ne, const float4 *stage, Acc<TB> 
 // (warp w of a block takes chunks w, w + nw, ...).
 template <int TB>
 __device__ __forceinline__ void accumulate(const uint32_t *__restrict__ evp, int cnt, int chunk0,
-                                           int chunk_step, const GridConst &g, uint64_t arow_mod,
+                                           int chunk_step, const GridConst &g,
+                                           const uint64_t (&arow_mod)[2],
                                            float4 *stage, Acc<TB> &acc) {
   for (int c0 = chunk0 * kGenChunk; c0 < cnt; c0 += chunk_step * kGenChunk) {
     const int ne = min(kGenChunk, cnt - c0);
@@ -164,8 +182,10 @@ __device__ __forceinline__ void finalize_tile(const Acc<TB> &acc, float *Pw, int
     float pv[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const float fr = __fsub_rn(acc.t1[i][q], acc.t2[i][q]);
-      const float fi = __fsub_rn(__fsub_rn(acc.t3[i][q], acc.t1[i][q]), acc.t2[i][q]);
+      const float t1 = acc.get(acc.t1, i, q), t2 = acc.get(acc.t2, i, q);
+      const float t3 = acc.get(acc.t3, i, q);
+      const float fr = __fsub_rn(t1, t2);
+      const float fi = __fsub_rn(__fsub_rn(t3, t1), t2);
       pv[q] = __fmaf_rn(fr, fr, __fmul_rn(fi, fi));
     }
     const int row = row_base + bg * TB + i;
@@ -202,7 +222,8 @@ __device__ __forceinline__ void pixel_spectrum_warp(const BlockedArgs &A, const 
   const GridConst &g = A.g;
   const int rows_per_pass = 4 * TB;
   for (int b0 = 0; b0 < g.nbr; b0 += rows_per_pass) {
-    const uint64_t arow_mod = (g.a0 + (uint64_t)(32 * b0) * g.da) % g.denom;
+    const uint64_t arow_mod[2] = {(g.a0 + (uint64_t)(32 * b0) * g.da) % g.denom,
+                                  (g.a0 + (uint64_t)(32 * (b0 + 2 * TB)) * g.da) % g.denom};
     Acc<TB> acc;
     acc.zero();
     accumulate<TB>(evp, cnt, 0, 1, g, arow_mod, stage, acc);
@@ -261,7 +282,9 @@ __global__ void k_blocked(BlockedArgs A) {
       continue;
     }
     for (int b0 = 0; b0 < A.g.nbr; b0 += rows_per_pass) {
-      const uint64_t arow_mod = (A.g.a0 + (uint64_t)(32 * b0) * A.g.da) % A.g.denom;
+      const uint64_t arow_mod[2] = {
+          (A.g.a0 + (uint64_t)(32 * b0) * A.g.da) % A.g.denom,
+          (A.g.a0 + (uint64_t)(32 * (b0 + 2 * TB)) * A.g.da) % A.g.denom};
       Acc<TB> acc;
       acc.zero();
       accumulate<TB>(v.ev + o0, cnt, warp, nw, A.g, arow_mod, stage, acc);
@@ -271,9 +294,9 @@ __global__ void k_blocked(BlockedArgs A) {
       for (int i = 0; i < TB; ++i)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          part[((0 * TB + i) * 4 + q) * 32 + lane] = acc.t1[i][q];
-          part[((1 * TB + i) * 4 + q) * 32 + lane] = acc.t2[i][q];
-          part[((2 * TB + i) * 4 + q) * 32 + lane] = acc.t3[i][q];
+          part[((0 * TB + i) * 4 + q) * 32 + lane] = acc.get(acc.t1, i, q);
+          part[((1 * TB + i) * 4 + q) * 32 + lane] = acc.get(acc.t2, i, q);
+          part[((2 * TB + i) * 4 + q) * 32 + lane] = acc.get(acc.t3, i, q);
         }
       __syncthreads();
       if (warp == 0) {
@@ -283,9 +306,11 @@ __global__ void k_blocked(BlockedArgs A) {
           for (int i = 0; i < TB; ++i)
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-              acc.t1[i][q] = __fadd_rn(acc.t1[i][q], op[((0 * TB + i) * 4 + q) * 32 + lane]);
-              acc.t2[i][q] = __fadd_rn(acc.t2[i][q], op[((1 * TB + i) * 4 + q) * 32 + lane]);
-              acc.t3[i][q] = __fadd_rn(acc.t3[i][q], op[((2 * TB + i) * 4 + q) * 32 + lane]);
+              float &x1 = acc.at(acc.t1, i, q), &x2 = acc.at(acc.t2, i, q);
+              float &x3 = acc.at(acc.t3, i, q);
+              x1 = __fadd_rn(x1, op[((0 * TB + i) * 4 + q) * 32 + lane]);
+              x2 = __fadd_rn(x2, op[((1 * TB + i) * 4 + q) * 32 + lane]);
+              x3 = __fadd_rn(x3, op[((2 * TB + i) * 4 + q) * 32 + lane]);
             }
         }
         if (FUSED) {

@@ -148,6 +148,7 @@ extern "C" ddhf_status ddhf_power_spectrum_noalloc(const ddhf_grid *grid, const 
   g.denom = (uint64_t)grid->denom;
   g.barrett = ~0ull / (uint64_t)grid->denom;
   g.da_mod = (uint64_t)grid->da % (uint64_t)grid->denom;
+  g.da16_mod = ((uint64_t)grid->da * 16ull) % (uint64_t)grid->denom;
   g.da32_mod = ((uint64_t)grid->da * 32ull) % (uint64_t)grid->denom;
   g.N = grid->n_bins;
   g.nbr = (grid->n_bins + 31) / 32;

@@ -312,7 +312,7 @@ def test_fused_equals_unfused_bitwise():
     s = synth.small_scene(41, W=64, H=48, n_noise=60_000, drone_px=150,
                           grid=synth.hz_grid(0, 2, 750))
     for heavy_min in (32, 1024):
-        c = ctx_for(s, heavy_min=heavy_min)
+        c = ctx_for(s, heavy_min=heavy_min, fuse=1)
         x, y, t, p = ddhf.events_to_device(s)
         bx, nb, mask = c.detect(x, y, t, p, s.t0, s.window_us, want_mask=True)
         sc = c.scores()
@@ -357,12 +357,17 @@ def test_batch_graph_equals_single_windows():
     nbx = torch.zeros(len(scenes), dtype=torch.int32, device="cuda")
     masks = torch.empty((len(scenes), W * H), dtype=torch.uint8, device="cuda")
     ddhf.ddhf_enable_stage_timing(cb.h, True)
-    for use_graph in (False, True, True):
+    for fuse, use_graph in ((1, False), (1, True), (1, True), (0, False), (0, True), (0, True)):
+        cb.set_tuning(fuse=fuse)
         boxes.fill_(-7)
         masks.fill_(3)
         ddhf.ddhf_detect_batch(cb.h, wins, boxes, cap, nbx, masks, use_graph=use_graph)
         times = ddhf.ddhf_stage_times(cb.h)
-        assert all(t > 0 for t in times[:3]) and times[3] == times[4] == 0.0  # fused
+        assert all(t > 0 for t in times[:3])
+        if fuse:
+            assert times[3] == times[4] == 0.0
+        else:
+            assert times[3] > 0 and times[4] > 0
         torch.cuda.synchronize()
         for i, (bref, mref) in enumerate(single):
             n = int(nbx[i].item())
