@@ -111,6 +111,7 @@ void derive_constants(Ctx *c) {
   k.da = (uint64_t)g.da;
   k.denom = (uint64_t)g.denom;
   k.barrett = ~0ull / (uint64_t)g.denom;
+  k.a0_mod = (uint64_t)g.a0 % (uint64_t)g.denom;
   k.da_mod = (uint64_t)g.da % (uint64_t)g.denom;
   k.da16_mod = ((uint64_t)g.da * 16ull) % (uint64_t)g.denom;
   k.da32_mod = ((uint64_t)g.da * 32ull) % (uint64_t)g.denom;

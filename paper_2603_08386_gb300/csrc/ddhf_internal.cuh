@@ -64,6 +64,7 @@ struct CombConst {
 struct GridConst {
   uint64_t a0, da, denom;
   uint64_t barrett;   // floor((2^64 - 1) / denom)
+  uint64_t a0_mod;    // a0 mod denom
   uint64_t da_mod;    // da mod denom
   uint64_t da16_mod;  // 16 da mod denom
   uint64_t da32_mod;  // 32 da mod denom

@@ -32,6 +32,12 @@ namespace blocked {
 
 constexpr int kGenChunk = 16;
 
+// (a of bin 32 b) mod D = (a0 + 32 b da) mod D, for b < 2^11 (the operand of
+// the reduction stays below 2^43).
+__device__ __forceinline__ uint64_t arow_residue(const GridConst &g, int b) {
+  return mod_barrett(g.a0_mod + (uint64_t)b * g.da32_mod, g.denom, g.barrett);
+}
+
 __device__ __forceinline__ void raise_flag(uint32_t *flags, uint32_t f) { atomicOr(flags, f); }
 
 // ---------------------------------------------------------------- blocked
@@ -206,12 +212,30 @@ struct BlockedArgs {
   CombConst cc;
   float *P;                  // spectra (write mode), rows in active order of slot 0
   int64_t ld;                // row stride of P in floats (>= N)
+  int vec_store;             // P and ld 16-byte aligned
   int64_t cap_px;
   int heavy_min;
   int warp_bytes;            // per-warp shared memory (bytes)
   int pw_offset;             // byte offset of the spectrum buffer inside a warp's area
   uint32_t *flags;
 };
+
+// Bins [j_begin, j_end) of spectrum row `prow` from Pw (bin j_begin at Pw[0])
+// to P, by 16-byte stores when rows are 16-byte aligned (j_begin is a
+// multiple of 32).
+__device__ __forceinline__ void store_row(const BlockedArgs &A, int64_t prow, int j_begin,
+                                          int j_end, const float *Pw) {
+  const int lane = threadIdx.x & 31;
+  float *dst = A.P + prow * A.ld + j_begin;
+  int j0 = j_begin;
+  if (A.vec_store) {
+    const int n4 = (j_end - j_begin) >> 2;
+    for (int i = lane; i < n4; i += 32)
+      reinterpret_cast<float4 *>(dst)[i] = reinterpret_cast<const float4 *>(Pw)[i];
+    j0 = j_begin + 4 * n4;
+  }
+  for (int j = j0 + lane; j < j_end; j += 32) dst[j - j_begin] = Pw[j - j_begin];
+}
 
 // One pixel's spectrum into Pw (fused: all passes, N padded) or streamed to P.
 template <int TB, bool FUSED>
@@ -222,8 +246,7 @@ __device__ __forceinline__ void pixel_spectrum_warp(const BlockedArgs &A, const 
   const GridConst &g = A.g;
   const int rows_per_pass = 4 * TB;
   for (int b0 = 0; b0 < g.nbr; b0 += rows_per_pass) {
-    const uint64_t arow_mod[2] = {(g.a0 + (uint64_t)(32 * b0) * g.da) % g.denom,
-                                  (g.a0 + (uint64_t)(32 * (b0 + 2 * TB)) * g.da) % g.denom};
+    const uint64_t arow_mod[2] = {arow_residue(g, b0), arow_residue(g, b0 + 2 * TB)};
     Acc<TB> acc;
     acc.zero();
     accumulate<TB>(evp, cnt, 0, 1, g, arow_mod, stage, acc);
@@ -233,7 +256,7 @@ __device__ __forceinline__ void pixel_spectrum_warp(const BlockedArgs &A, const 
       finalize_tile<TB>(acc, Pw, 0);
       __syncwarp();
       const int j_begin = 32 * b0, j_end = min(g.N, 32 * (b0 + rows_per_pass));
-      for (int j = j_begin + lane; j < j_end; j += 32) A.P[prow * A.ld + j] = Pw[j - j_begin];
+      store_row(A, prow, j_begin, j_end, Pw);
     }
     __syncwarp();
   }
@@ -282,9 +305,7 @@ __global__ void k_blocked(BlockedArgs A) {
       continue;
     }
     for (int b0 = 0; b0 < A.g.nbr; b0 += rows_per_pass) {
-      const uint64_t arow_mod[2] = {
-          (A.g.a0 + (uint64_t)(32 * b0) * A.g.da) % A.g.denom,
-          (A.g.a0 + (uint64_t)(32 * (b0 + 2 * TB)) * A.g.da) % A.g.denom};
+      const uint64_t arow_mod[2] = {arow_residue(A.g, b0), arow_residue(A.g, b0 + 2 * TB)};
       Acc<TB> acc;
       acc.zero();
       accumulate<TB>(v.ev + o0, cnt, warp, nw, A.g, arow_mod, stage, acc);
@@ -319,7 +340,7 @@ __global__ void k_blocked(BlockedArgs A) {
           finalize_tile<TB>(acc, Pw, 0);
           __syncwarp();
           const int j_begin = 32 * b0, j_end = min(A.g.N, 32 * (b0 + rows_per_pass));
-          for (int j = j_begin + lane; j < j_end; j += 32) A.P[a * A.ld + j] = Pw[j - j_begin];
+          store_row(A, a, j_begin, j_end, Pw);
         }
         __syncwarp();
       }
@@ -332,7 +353,9 @@ __global__ void k_blocked(BlockedArgs A) {
     __syncthreads();
   }
 
-  // ---------------- light pixels: one warp each, virtual index over slots x pixels
+  // ---------------- light pixels: one warp each, virtual index over slots x pixels.
+  // A warp grabs kGrab consecutive virtual pixels; lanes 0..kGrab-1 fetch
+  // their metadata in parallel, then the warp takes the pixels in order.
   const int64_t total = (int64_t)A.n_slots * A.npx;
   constexpr int kGrab = 4;
   for (;;) {
@@ -340,25 +363,41 @@ __global__ void k_blocked(BlockedArgs A) {
     if (lane == 0) v0 = atomicAdd(&A.cursors[1], (uint32_t)kGrab);
     v0 = __shfl_sync(0xffffffffu, v0, 0);
     if ((int64_t)v0 >= total) break;
+    int m_slot = A.slot0, m_cnt = -1;
+    int64_t m_a = 0;
+    uint32_t m_key = 0, m_o0 = 0;
+    const uint32_t *m_ev = nullptr;
+    if (lane < kGrab) {
+      const int64_t vi = (int64_t)v0 + lane;
+      if (vi < total) {
+        const int64_t q = A.n_slots == 1 ? 0 : vi / A.npx;
+        m_slot = A.slot0 + (int)q;
+        m_a = vi - q * A.npx;
+        const SlotView &v = A.views[m_slot];
+        if (m_a < (int64_t)v.counters[2]) {
+          m_key = v.active[m_a];
+          m_o0 = v.offsets[m_key];
+          m_cnt = (int)(v.offsets[m_key + 1] - m_o0);
+          m_ev = v.ev + m_o0;
+        }
+      }
+    }
     for (int q = 0; q < kGrab; ++q) {
-      const int64_t vi = (int64_t)v0 + q;
-      if (vi >= total) break;
-      const int slot = A.slot0 + (int)(vi / A.npx);
-      const int64_t a = vi - (int64_t)(slot - A.slot0) * A.npx;
-      const SlotView v = A.views[slot];
-      if (a >= (int64_t)v.counters[2]) continue;
-      const uint32_t key = v.active[a];
-      const uint32_t o0 = v.offsets[key];
-      const int cnt = (int)(v.offsets[key + 1] - o0);
-      if (cnt >= A.heavy_min) continue;
+      const int cnt = __shfl_sync(0xffffffffu, m_cnt, q);
+      const int slot = __shfl_sync(0xffffffffu, m_slot, q);
+      const int64_t a = __shfl_sync(0xffffffffu, m_a, q);
+      const uint32_t key = __shfl_sync(0xffffffffu, m_key, q);
+      const uint32_t *evp = reinterpret_cast<const uint32_t *>(
+          __shfl_sync(0xffffffffu, reinterpret_cast<uintptr_t>(m_ev), q));
+      if (cnt < 0 || cnt >= A.heavy_min) continue;  // inactive, past the end, or heavy
       if (!FUSED && a >= A.cap_px) {
         if (lane == 0) raise_flag(A.flags, DDHF_FLAG_CAPACITY);
         continue;
       }
-      pixel_spectrum_warp<TB, FUSED>(A, v.ev + o0, cnt, a, stage, Pw);
+      pixel_spectrum_warp<TB, FUSED>(A, evp, cnt, a, stage, Pw);
       if (FUSED) {
         CombOut o = comb_warp<NW>(Pw, A.cc, reinterpret_cast<unsigned char *>(stage));
-        store_scores<NW>(A, v, a, key, o);
+        store_scores<NW>(A, A.views[slot], a, key, o);
       }
     }
   }
@@ -397,6 +436,7 @@ ddhf_status launch_blocked_t(Ctx *c, int n_slots, float *P, int64_t cap_px, cuda
   A.cc = c->comb;
   A.P = P;
   A.ld = ld > 0 ? ld : c->gconst.N;
+  A.vec_store = (A.ld % 4 == 0) && (reinterpret_cast<uintptr_t>(P) % 16 == 0);
   A.cap_px = cap_px;
   A.heavy_min = c->tuning.heavy_min;
   A.warp_bytes = blocked_warp_bytes<TB>(c, FUSED, NW, &A.pw_offset);

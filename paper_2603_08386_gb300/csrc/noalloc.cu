@@ -86,6 +86,7 @@ ddhf_status launch_noalloc(NoAllocScratch *sp, const GridConst &g, float *P, int
   A.cc = CombConst{};
   A.P = P;
   A.ld = g.N;
+  A.vec_store = (A.ld % 4 == 0) && (reinterpret_cast<uintptr_t>(P) % 16 == 0);
   A.cap_px = cap_px;
   A.heavy_min = kNoAllocHeavyMin;
   const int stage = blocked::WarpLayout<TB>::kStageF4 * 16;
@@ -147,6 +148,7 @@ extern "C" ddhf_status ddhf_power_spectrum_noalloc(const ddhf_grid *grid, const 
   g.da = (uint64_t)grid->da;
   g.denom = (uint64_t)grid->denom;
   g.barrett = ~0ull / (uint64_t)grid->denom;
+  g.a0_mod = (uint64_t)grid->a0 % (uint64_t)grid->denom;
   g.da_mod = (uint64_t)grid->da % (uint64_t)grid->denom;
   g.da16_mod = ((uint64_t)grid->da * 16ull) % (uint64_t)grid->denom;
   g.da32_mod = ((uint64_t)grid->da * 32ull) % (uint64_t)grid->denom;
