@@ -58,21 +58,20 @@ struct WarpLayout {
   static constexpr int kStageF4 = kA + kGenChunk * ALayout<TB>::kEvent;
 };
 
-// Generate the A and B factors of events [0, ne) of one chunk (evp points at
-// the chunk's first event). Two lanes per event run the same code: lane e
-// (half 0) writes B columns r = 0..15 and A rows 0..2TB-1, lane e + 16
-// (half 1) B columns 16..31 and A rows 2TB..4TB-1, each from exact seeds
-// (residues of its first column / row) stepped by the exact unit phasors
-// u = e^{-2 pi i da tau / D} (columns) and u^32 (rows).
+// Generate the A and B factors of the events of one chunk; w is the event
+// word of event e = lane % 16, active when e < the chunk's event count. Two
+// lanes per event run the same code: lane e (half 0) writes B columns
+// r = 0..15 and A rows 0..2TB-1, lane e + 16 (half 1) B columns 16..31 and A
+// rows 2TB..4TB-1, each from exact seeds (residues of its first column / row)
+// stepped by the unit phasors u = e^{-2 pi i da tau / D} (columns) and u^32
+// (rows), in two interleaved chains each.
 // arow_mod[h]: (a of the first A row of half h) mod D.
 template <int TB>
-__device__ __forceinline__ void gen_chunk(const uint32_t *__restrict__ evp, int ne,
-                                          const GridConst &g, const uint64_t (&arow_mod)[2],
-                                          float4 *stage) {
+__device__ __forceinline__ void gen_chunk(uint32_t w, bool active, const GridConst &g,
+                                          const uint64_t (&arow_mod)[2], float4 *stage) {
   const int lane = threadIdx.x & 31;
   const int e = lane & 15, half = lane >> 4;
-  if (e >= ne) return;
-  const uint32_t w = evp[e];
+  if (!active) return;
   const uint64_t tau = w & 0x7fffffffu;
   const uint64_t rz = mod_barrett((half ? g.da16_mod : 0ull) * tau, g.denom, g.barrett);
   const uint64_t ru = mod_barrett(g.da_mod * tau, g.denom, g.barrett);
@@ -87,29 +86,38 @@ __device__ __forceinline__ void gen_chunk(const uint32_t *__restrict__ evp, int 
     s.x = -s.x;
     s.y = -s.y;
   }
+  // columns: two interleaved chains (even and odd r) stepped by u^2
+  const float2 u2 = cmul(u, u);
+  float2 za = z, zb = cmul(z, u);
   float4 *dstb = stage + WarpLayout<TB>::kB + e * kBEvent + half * 4 * 3;
 #pragma unroll
   for (int rg = 0; rg < 4; ++rg) {
-    float br[4], bi[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      br[q] = z.x;
-      bi[q] = z.y;
-      if (rg < 3 || q < 3) z = cmul(z, u);
+    const float2 zc = cmul(za, u2), zd = cmul(zb, u2);
+    const float br[4] = {za.x, zb.x, zc.x, zd.x};
+    const float bi[4] = {za.y, zb.y, zc.y, zd.y};
+    if (rg < 3) {
+      za = cmul(zc, u2);
+      zb = cmul(zd, u2);
     }
     dstb[rg * 3 + 0] = make_float4(br[0], br[1], br[2], br[3]);
     dstb[rg * 3 + 1] = make_float4(bi[0], bi[1], bi[2], bi[3]);
     dstb[rg * 3 + 2] = make_float4(__fadd_rn(br[0], bi[0]), __fadd_rn(br[1], bi[1]),
                                    __fadd_rn(br[2], bi[2]), __fadd_rn(br[3], bi[3]));
   }
+  // rows: two interleaved chains (even and odd row) stepped by v^2
+  const float2 v2 = cmul(v, v);
+  float2 sa = s, sb = cmul(s, v);
   float4 *dsta = stage + WarpLayout<TB>::kA + e * ALayout<TB>::kEvent +
                  half * 2 * ALayout<TB>::kGroup;
 #pragma unroll
-  for (int bg = 0; bg < 2; ++bg) {
-#pragma unroll
-    for (int i = 0; i < TB; ++i) {
-      dsta[bg * ALayout<TB>::kGroup + i] = make_float4(s.x, s.y, __fadd_rn(s.x, s.y), 0.f);
-      if (bg < 1 || i < TB - 1) s = cmul(s, v);
+  for (int k = 0; k < 2 * TB; k += 2) {
+    dsta[(k / TB) * ALayout<TB>::kGroup + k % TB] =
+        make_float4(sa.x, sa.y, __fadd_rn(sa.x, sa.y), 0.f);
+    dsta[((k + 1) / TB) * ALayout<TB>::kGroup + (k + 1) % TB] =
+        make_float4(sb.x, sb.y, __fadd_rn(sb.x, sb.y), 0.f);
+    if (k + 2 < 2 * TB) {
+      sa = cmul(sa, v2);
+      sb = cmul(sb, v2);
     }
   }
 }
@@ -169,10 +177,16 @@ __device__ __forceinline__ void accumulate(const uint32_t *__restrict__ evp, int
                                            int chunk_step, const GridConst &g,
                                            const uint64_t (&arow_mod)[2],
                                            float4 *stage, Acc<TB> &acc) {
-  for (int c0 = chunk0 * kGenChunk; c0 < cnt; c0 += chunk_step * kGenChunk) {
+  const int e = threadIdx.x & 15;
+  const int step = chunk_step * kGenChunk;
+  int c0 = chunk0 * kGenChunk;
+  uint32_t w = c0 + e < cnt ? evp[c0 + e] : 0u;
+  for (; c0 < cnt; c0 += step) {
     const int ne = min(kGenChunk, cnt - c0);
-    gen_chunk<TB>(evp + c0, ne, g, arow_mod, stage);
+    gen_chunk<TB>(w, e < ne, g, arow_mod, stage);
     __syncwarp();
+    const int c1 = c0 + step;  // the next chunk's event word, loaded ahead
+    w = c1 + e < cnt ? evp[c1 + e] : 0u;
     gemm_chunk<TB>(ne, stage, acc);
     __syncwarp();
   }
