@@ -17,9 +17,9 @@
 //                   u_k). The product is accumulated with three real
 //                   multiplications per term (T1 = sum Ar Br, T2 = sum Ai Bi,
 //                   T3 = sum (Ar+Ai)(Br+Bi); Re F = T1 - T2, Im F = T3 - T1
-//                   - T2). Lanes hold a TB x 4 tile of (b, r) accumulators;
-//                   events are generated 16 at a time into shared memory by
-//                   16 "B" lanes and 16 "A" lanes. Light pixels take one warp,
+//                   - T2). Lanes hold a TB x 4 tile of (b, r) accumulators,
+//                   updated by paired FMAs; events are generated 16 at a time
+//                   into shared memory, two lanes per event. Light pixels take one warp,
 //                   heavy pixels a whole block (events split over warps,
 //                   partial sums reduced in a fixed order), heavy first.
 #pragma once
@@ -99,8 +99,8 @@ __device__ __forceinline__ void gen_chunk(uint32_t w, bool active, const GridCon
       za = cmul(zc, u2);
       zb = cmul(zd, u2);
     }
-    dstb[rg * 3 + 0] = make_float4(br[0], br[1], br[2], br[3]);
-    dstb[rg * 3 + 1] = make_float4(bi[0], bi[1], bi[2], bi[3]);
+    dstb[rg * 3 + 0] = make_float4(br[0], bi[0], br[1], bi[1]);
+    dstb[rg * 3 + 1] = make_float4(br[2], bi[2], br[3], bi[3]);
     dstb[rg * 3 + 2] = make_float4(__fadd_rn(br[0], bi[0]), __fadd_rn(br[1], bi[1]),
                                    __fadd_rn(br[2], bi[2]), __fadd_rn(br[3], bi[3]));
   }
@@ -111,10 +111,9 @@ __device__ __forceinline__ void gen_chunk(uint32_t w, bool active, const GridCon
                  half * 2 * ALayout<TB>::kGroup;
 #pragma unroll
   for (int k = 0; k < 2 * TB; k += 2) {
-    dsta[(k / TB) * ALayout<TB>::kGroup + k % TB] =
-        make_float4(sa.x, sa.y, __fadd_rn(sa.x, sa.y), 0.f);
-    dsta[((k + 1) / TB) * ALayout<TB>::kGroup + (k + 1) % TB] =
-        make_float4(sb.x, sb.y, __fadd_rn(sb.x, sb.y), 0.f);
+    const float ssa = __fadd_rn(sa.x, sa.y), ssb = __fadd_rn(sb.x, sb.y);
+    dsta[(k / TB) * ALayout<TB>::kGroup + k % TB] = make_float4(sa.x, sa.y, ssa, ssa);
+    dsta[((k + 1) / TB) * ALayout<TB>::kGroup + (k + 1) % TB] = make_float4(sb.x, sb.y, ssb, ssb);
     if (k + 2 < 2 * TB) {
       sa = cmul(sa, v2);
       sb = cmul(sb, v2);
@@ -122,23 +121,33 @@ __device__ __forceinline__ void gen_chunk(uint32_t w, bool active, const GridCon
   }
 }
 
-// Accumulators of a lane's TB x 4 tile, bins (q, q + 1) of a row packed in a
-// float2 so that one paired FMA (FFMA2, each element rounded on its own)
-// serves two bins.
+// Accumulators of a lane's TB x 4 tile, in float2 pairs so that one paired
+// FMA (FFMA2, each element rounded on its own) updates two of them:
+// t12[i][q] = (T1, T2) of bin (i, q), t3[i][h] = (T3 of bin (i, 2h), of (i, 2h+1)).
+// Shared-memory operands come in matching pairs: A rows as (Ar, Ai, Ar+Ai,
+// Ar+Ai), B columns as (Br0, Bi0, Br1, Bi1), (Br2, Bi2, Br3, Bi3),
+// (Br0+Bi0, .., Br3+Bi3).
 template <int TB>
 struct Acc {
-  float2 t1[TB][2], t2[TB][2], t3[TB][2];
+  float2 t12[TB][4], t3[TB][2];
   __device__ __forceinline__ void zero() {
 #pragma unroll
-    for (int i = 0; i < TB; ++i)
+    for (int i = 0; i < TB; ++i) {
 #pragma unroll
-      for (int h = 0; h < 2; ++h) t1[i][h] = t2[i][h] = t3[i][h] = make_float2(0.f, 0.f);
+      for (int q = 0; q < 4; ++q) t12[i][q] = make_float2(0.f, 0.f);
+      t3[i][0] = t3[i][1] = make_float2(0.f, 0.f);
+    }
   }
-  __device__ __forceinline__ float &at(float2 (&t)[TB][2], int i, int q) {
-    return (q & 1) ? t[i][q >> 1].y : t[i][q >> 1].x;
+  // component c (0: T1, 1: T2, 2: T3) of bin (i, q)
+  __device__ __forceinline__ float &at(int c, int i, int q) {
+    if (c == 0) return t12[i][q].x;
+    if (c == 1) return t12[i][q].y;
+    return (q & 1) ? t3[i][q >> 1].y : t3[i][q >> 1].x;
   }
-  __device__ __forceinline__ float get(const float2 (&t)[TB][2], int i, int q) const {
-    return (q & 1) ? t[i][q >> 1].y : t[i][q >> 1].x;
+  __device__ __forceinline__ float get(int c, int i, int q) const {
+    if (c == 0) return t12[i][q].x;
+    if (c == 1) return t12[i][q].y;
+    return (q & 1) ? t3[i][q >> 1].y : t3[i][q >> 1].x;
   }
 };
 
@@ -149,23 +158,20 @@ __device__ __forceinline__ void gemm_chunk(int ne, const float4 *stage, Acc<TB> 
   const float4 *sb = stage + WarpLayout<TB>::kB + rg * 3;
   const float4 *sa = stage + WarpLayout<TB>::kA + bg * ALayout<TB>::kGroup;
   for (int e = 0; e < ne; ++e) {
-    const float4 br = sb[e * kBEvent + 0];
-    const float4 bi = sb[e * kBEvent + 1];
+    const float4 b01 = sb[e * kBEvent + 0];
+    const float4 b23 = sb[e * kBEvent + 1];
     const float4 bs = sb[e * kBEvent + 2];
-    const float2 brr[2] = {make_float2(br.x, br.y), make_float2(br.z, br.w)};
-    const float2 bii[2] = {make_float2(bi.x, bi.y), make_float2(bi.z, bi.w)};
+    const float2 bri[4] = {make_float2(b01.x, b01.y), make_float2(b01.z, b01.w),
+                           make_float2(b23.x, b23.y), make_float2(b23.z, b23.w)};
     const float2 bss[2] = {make_float2(bs.x, bs.y), make_float2(bs.z, bs.w)};
 #pragma unroll
     for (int i = 0; i < TB; ++i) {
       const float4 a = sa[e * ALayout<TB>::kEvent + i];
-      const float2 ax = make_float2(a.x, a.x), ay = make_float2(a.y, a.y);
-      const float2 az = make_float2(a.z, a.z);
+      const float2 axy = make_float2(a.x, a.y), ass = make_float2(a.z, a.w);
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        acc.t1[i][h] = __ffma2_rn(ax, brr[h], acc.t1[i][h]);
-        acc.t2[i][h] = __ffma2_rn(ay, bii[h], acc.t2[i][h]);
-        acc.t3[i][h] = __ffma2_rn(az, bss[h], acc.t3[i][h]);
-      }
+      for (int q = 0; q < 4; ++q) acc.t12[i][q] = __ffma2_rn(axy, bri[q], acc.t12[i][q]);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) acc.t3[i][h] = __ffma2_rn(ass, bss[h], acc.t3[i][h]);
     }
   }
 }
@@ -202,8 +208,7 @@ __device__ __forceinline__ void finalize_tile(const Acc<TB> &acc, float *Pw, int
     float pv[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const float t1 = acc.get(acc.t1, i, q), t2 = acc.get(acc.t2, i, q);
-      const float t3 = acc.get(acc.t3, i, q);
+      const float t1 = acc.get(0, i, q), t2 = acc.get(1, i, q), t3 = acc.get(2, i, q);
       const float fr = __fsub_rn(t1, t2);
       const float fi = __fsub_rn(__fsub_rn(t3, t1), t2);
       pv[q] = __fmaf_rn(fr, fr, __fmul_rn(fi, fi));
@@ -329,9 +334,9 @@ __global__ void k_blocked(BlockedArgs A) {
       for (int i = 0; i < TB; ++i)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          part[((0 * TB + i) * 4 + q) * 32 + lane] = acc.get(acc.t1, i, q);
-          part[((1 * TB + i) * 4 + q) * 32 + lane] = acc.get(acc.t2, i, q);
-          part[((2 * TB + i) * 4 + q) * 32 + lane] = acc.get(acc.t3, i, q);
+          part[((0 * TB + i) * 4 + q) * 32 + lane] = acc.get(0, i, q);
+          part[((1 * TB + i) * 4 + q) * 32 + lane] = acc.get(1, i, q);
+          part[((2 * TB + i) * 4 + q) * 32 + lane] = acc.get(2, i, q);
         }
       __syncthreads();
       if (warp == 0) {
@@ -341,8 +346,8 @@ __global__ void k_blocked(BlockedArgs A) {
           for (int i = 0; i < TB; ++i)
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-              float &x1 = acc.at(acc.t1, i, q), &x2 = acc.at(acc.t2, i, q);
-              float &x3 = acc.at(acc.t3, i, q);
+              float &x1 = acc.at(0, i, q), &x2 = acc.at(1, i, q);
+              float &x3 = acc.at(2, i, q);
               x1 = __fadd_rn(x1, op[((0 * TB + i) * 4 + q) * 32 + lane]);
               x2 = __fadd_rn(x2, op[((1 * TB + i) * 4 + q) * 32 + lane]);
               x3 = __fadd_rn(x3, op[((2 * TB + i) * 4 + q) * 32 + lane]);
@@ -430,6 +435,12 @@ int blocked_warp_bytes(const Ctx *c, bool fused, int NW, int *pw_offset) {
     if (cb > scratch) scratch = cb;
   }
   scratch = (scratch + 15) & ~15;
+  if (!fused) {
+    // the tile of one pass is written after that pass's last GEMM step and
+    // streamed out before the next generation step: it shares the staging area
+    *pw_offset = 0;
+    return scratch > pw ? scratch : pw;
+  }
   *pw_offset = scratch;
   return scratch + pw;
 }
