@@ -29,6 +29,13 @@ __global__ void __launch_bounds__(128, NW == 0 ? 7 : 1) k_comb(const float *__re
   const int N = cc.N;
   for (int64_t a = wid; a < n_active && a < cap_px; a += nwarps) {
     const float *row = P + a * ld;
+    if (vec && lane == 0 && a + nwarps < n_active && a + nwarps < cap_px) {
+      // the warp's next row into L2 while this one is scored
+      const float *nxt = P + (a + nwarps) * ld;
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(nxt),
+                   "r"((uint32_t)(((N + 3) / 4) * 16))
+                   : "memory");
+    }
     if (vec) {
       const float4 *r4 = reinterpret_cast<const float4 *>(row);
       const int n4 = (N + 3) / 4;
