@@ -207,6 +207,8 @@ def main():
                     help="windows per step (default 32; fewer only for profiling cases)")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default tuning)")
     ap.add_argument("--procs", type=int, default=int(os.environ.get("DDHF_GEN_PROCS", "16")))
+    ap.add_argument("--no-latency", action="store_true", help="skip the one-window latency")
+    ap.add_argument("--latency-replays", type=int, default=100)
     ap.add_argument("--sensor", default="1280x720",
                     help="WxH of the synthetic sensor (smaller sizes for profiling captures)")
     args = ap.parse_args()
@@ -319,6 +321,31 @@ def main():
         e2e_ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
         e2e = dict(value=job_throughput(terms_step, world, e2e_steps, e2e_ms), unit=UNIT,
                    h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h, steps=e2e_steps)
+    # ------------------------------------------------------------ one-window latency
+    # a single 1280x720 window (stream 0, window 0) through the graph-replayed
+    # detection call, each replay timed on its own, after the bench's tuning
+    lat = None
+    if not args.no_latency:
+        lc = ddhf.Context(W, H, grid, max_events=max_ev, max_windows=1)
+        lc.set_tuning(**{k: v for k, v in tuning.items() if k != "how"})
+        lb = torch.empty((cap, 5), dtype=torch.int32, device="cuda")
+        ln = torch.zeros(1, dtype=torch.int32, device="cuda")
+        for _ in range(5):
+            ddhf.ddhf_detect_batch(lc.h, wl[:1], lb, cap, ln, None, use_graph=True)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.latency_replays)]
+        for a, b in evs:
+            a.record()
+            ddhf.ddhf_detect_batch(lc.h, wl[:1], lb, cap, ln, None, use_graph=True)
+            b.record()
+        torch.cuda.synchronize()
+        lt = np.array([a.elapsed_time(b) for a, b in evs])
+        q25, q50, q75, q95 = np.percentile(lt, [25, 50, 75, 95])
+        lat = dict(window="stream 0, window 0 (one 30 ms window of the batch)",
+                   events=int(wins[0][6]), replays=len(lt), median_ms=float(q50),
+                   iqr_ms=float(q75 - q25), p95_ms=float(q95), min_ms=float(lt.min()))
+        lc.close()
     # ------------------------------------------------------------ plain per-pixel pipeline
     plain = None
     if not args.no_plain:
@@ -393,6 +420,7 @@ def main():
                           "product); peak = 152 SMs x 128 FP32 lanes x 2070 MHz",
                       comb_kernel_ms_per_step=None if fused_mode else statistics.mean(comb_ms)),
         e2e=e2e,
+        window_latency=lat,
         gpu_launches=int(graph_kernels) * args.steps,
         clocks=clk,
         plain=plain,

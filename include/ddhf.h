@@ -240,8 +240,10 @@ ddhf_status ddhf_boxes(ddhf_ctx *ctx, const int32_t *labels, ddhf_box *boxes, in
                        int32_t *n_boxes_dev, ddhf_stream stream);
 
 /* The whole per-window pipeline of Sec. 3.5 on one window: binning, the
- * BLOCKED NDFT with SF and comb scoring fused into it (spectra stay on chip),
- * labelling and boxes. mask_out[W*H] (nullable) receives the rotor mask. */
+ * BLOCKED NDFT spectra and the SF + comb scoring (as separate kernels through
+ * a context buffer, or fused so that spectra stay on chip, per the tuning's
+ * fuse flag), labelling and boxes. mask_out[W*H] (nullable) receives the
+ * rotor mask. */
 ddhf_status ddhf_detect(ddhf_ctx *ctx, const int16_t *x, const int16_t *y,
                         const int64_t *t_us, const int8_t *p, int64_t n, int64_t t0_us,
                         int64_t window_us, ddhf_box *boxes, int32_t cap,
@@ -328,6 +330,53 @@ ddhf_status ddhf_power_spectrum_noalloc(const ddhf_grid *grid, const uint32_t *o
                                         const uint32_t *ev, int64_t n_events,
                                         const uint32_t *active, int64_t n_active, float *P,
                                         int64_t cap_px, ddhf_stream stream);
+
+/* ---------------------------------------------------------------- row bands
+ * The per-pixel steps (binning, Eq. 6-11) are independent per pixel, so a
+ * sensor can be split into row bands processed by separate contexts (one per
+ * GPU). Only the segmentation of Sec. 3.5 couples the bands: components that
+ * cross a band boundary are joined through the labels of the two boundary
+ * rows, then the area filter and the Eq. 12 merge run once on the joined
+ * components. The paper describes a single device; this is the same
+ * computation split by rows. */
+
+/* One connected component of a band's rotor mask in sensor coordinates:
+ * label = smallest sensor linear index y*W_sensor + x of its pixels,
+ * inclusive bounding box, pixel count. */
+typedef struct {
+  int32_t label, x0, y0, x1, y1, n_px;
+} ddhf_component;
+
+/* Make the context a row band: its rows 0..H-1 are sensor rows row0..row0+H-1.
+ * Binning then keeps events with row0 <= y < row0 + H (others are dropped and
+ * counted), and pixel keys and outputs stay band-local. row0 >= 0. */
+ddhf_status ddhf_set_row_offset(ddhf_ctx *ctx, int32_t row0);
+
+/* Components of labels[W*H] (as ddhf_label writes them, band-local) with no
+ * area filter and no merging, in sensor coordinates for a band whose row 0 is
+ * sensor row row0 (labels and y shifted by row0 * W and row0). Order is
+ * unspecified. comps[cap] device array; *n_dev (device int32) gets the total,
+ * which may exceed cap. */
+ddhf_status ddhf_components(ddhf_ctx *ctx, const int32_t *labels, int32_t row0,
+                            ddhf_component *comps, int32_t cap, int32_t *n_dev,
+                            ddhf_stream stream);
+
+/* Host-only: the boxes of a W x H sensor split into n_bands row bands, equal
+ * to what ddhf_boxes gives on the whole sensor's labels. Band b covers rows
+ * [band_row0[b], band_row0[b+1]) (band_row0 has n_bands + 1 entries,
+ * increasing, from 0 to H). edge_labels[b*2*W + k*W + x] is band b's own
+ * label (band-local, as ddhf_label writes it; -1 for background) of its first
+ * (k = 0) and last (k = 1) row at column x. comps holds every band's
+ * components (as ddhf_components writes them, in sensor coordinates),
+ * band b's at comps[comp_off[b] .. comp_off[b+1]). Components touching
+ * across a boundary (8-connected) are joined; boxes with area < A_min are
+ * removed; Eq. 12 merging is repeated to a fixed point with params->alpha;
+ * output sorted by (y0, x0, y1, x1, n_px) into boxes[cap], the total in
+ * *n_boxes (may exceed cap). All pointers are host memory. */
+ddhf_status ddhf_merge_bands(int32_t W, int32_t H, int32_t n_bands, const int32_t *band_row0,
+                             const int32_t *edge_labels, const ddhf_component *comps,
+                             const int64_t *comp_off, const ddhf_params *params,
+                             ddhf_box *boxes, int32_t cap, int32_t *n_boxes);
 
 /* Synchronise the context's last stream and read its counters and device
  * flags. Returns DDHF_ERR_CAPACITY / DDHF_ERR_TIMEOUT when the matching

@@ -535,6 +535,29 @@ ddhf_status ddhf_boxes(ddhf_ctx *h, const int32_t *labels, ddhf_box *boxes, int3
   return launch_boxes(c, labels, boxes, cap, n_boxes_dev, s);
 }
 
+ddhf_status ddhf_set_row_offset(ddhf_ctx *h, int32_t row0) {
+  if (!h) return DDHF_ERR_INVALID_ARG;
+  Ctx *c = &h->c;
+  if (row0 < 0 || (int64_t)row0 + c->H > 32767)
+    return fail(c, DDHF_ERR_INVALID_ARG, "row offset out of range");
+  c->row0 = row0;
+  drop_graph(c);
+  return DDHF_OK;
+}
+
+ddhf_status ddhf_components(ddhf_ctx *h, const int32_t *labels, int32_t row0,
+                            ddhf_component *comps, int32_t cap, int32_t *n_dev,
+                            ddhf_stream stream) {
+  if (!h) return DDHF_ERR_INVALID_ARG;
+  Ctx *c = &h->c;
+  if (!labels || !n_dev || cap < 0 || (cap > 0 && !comps) || row0 < 0 ||
+      (int64_t)row0 * c->W + c->npx > INT32_MAX)
+    return fail(c, DDHF_ERR_INVALID_ARG, "bad component arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  return launch_components(c, labels, row0, comps, cap, n_dev, s);
+}
+
 ddhf_status ddhf_detect(ddhf_ctx *h, const int16_t *x, const int16_t *y, const int64_t *t_us,
                         const int8_t *p, int64_t n, int64_t t0_us, int64_t window_us,
                         ddhf_box *boxes, int32_t cap, int32_t *n_boxes_dev, uint8_t *mask_out,

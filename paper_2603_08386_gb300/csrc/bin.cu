@@ -30,11 +30,12 @@ struct RawIn {
   int64_t t0;
   uint64_t win;
   int W, H, pol01;
+  int row0;  // sensor row of the context's row 0 (row bands)
 };
 
 __device__ __forceinline__ bool load_raw(const RawIn &in, int64_t e, uint32_t &key,
                                          uint32_t &val) {
-  int xx = in.x[e], yy = in.y[e];
+  int xx = in.x[e], yy = in.y[e] - in.row0;
   int64_t tt = in.t[e];
   int pp = in.p[e];
   bool okp = in.pol01 ? (pp == 0 || pp == 1) : (pp == 1 || pp == -1);
@@ -313,7 +314,7 @@ ddhf_status bin_window(Ctx *c, int slot_i, const int16_t *x, const int16_t *y, c
   uint32_t *ntot = reinterpret_cast<uint32_t *>(c->qctl + 8);  // n_valid of this binning
   DDHF_CUDA_TRY(c, cudaMemsetAsync(ntot, 0, sizeof(uint32_t), s));
   DDHF_CUDA_TRY(c, cudaMemsetAsync(sl.counters, 0, 7 * sizeof(uint64_t), s));
-  RawIn raw{x, y, t, p, n, t0, (uint64_t)win, c->W, c->H, c->params.polarity_01};
+  RawIn raw{x, y, t, p, n, t0, (uint64_t)win, c->W, c->H, c->params.polarity_01, c->row0};
   const int64_t nch = ceil_div(n, kBinChunk);
   uint32_t *kbuf[2] = {c->keysA, c->keysB};
   uint32_t *vbuf[2] = {c->valsA, c->valsB};

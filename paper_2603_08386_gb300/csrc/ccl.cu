@@ -158,6 +158,26 @@ __global__ void k_box_collect(const int32_t *__restrict__ lab, const int32_t *__
   }
 }
 
+// Every component (no area filter), shifted to sensor coordinates.
+__global__ void k_comp_collect(const int32_t *__restrict__ lab, const int32_t *__restrict__ bx,
+                               int64_t npx, int W, int32_t row0, ddhf_component *out, int cap,
+                               uint32_t *count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npx;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (lab[i] != (int32_t)i) continue;
+    const uint32_t pos = atomicAdd(count, 1u);
+    if ((int64_t)pos >= cap) continue;
+    ddhf_component c;
+    c.label = (int32_t)(i + (int64_t)row0 * W);
+    c.x0 = bx[i];
+    c.y0 = bx[npx + i] + row0;
+    c.x1 = bx[2 * npx + i];
+    c.y1 = bx[3 * npx + i] + row0;
+    c.n_px = bx[4 * npx + i];
+    out[pos] = c;
+  }
+}
+
 // Eq. 12 in FP64, every product rounded on its own.
 __device__ __forceinline__ bool eq12_close(const int32_t *a, const int32_t *b, double alpha) {
   const int64_t dx2 = (int64_t)(a[0] + a[2]) - (int64_t)(b[0] + b[2]);
@@ -328,6 +348,20 @@ ddhf_status launch_label(Ctx *c, const uint8_t *mask, int32_t *labels, uint64_t 
   k_label_init<<<blocks, 256, 0, s>>>(mask, labels, c->npx, nfg);
   k_label_union<<<blocks, 256, 0, s>>>(mask, labels, c->W, c->H, c->flags);
   k_label_compress<<<blocks, 256, 0, s>>>(labels, c->npx, c->flags);
+  DDHF_CUDA_TRY(c, cudaGetLastError());
+  return DDHF_OK;
+}
+
+ddhf_status launch_components(Ctx *c, const int32_t *labels, int32_t row0, ddhf_component *out,
+                              int32_t cap, int32_t *n_out, cudaStream_t s) {
+  const int blocks = c->num_sms * 8;
+  const int64_t npx = c->npx;
+  int32_t *bx = c->box_tmp;  // 5 * npx
+  uint32_t *count = reinterpret_cast<uint32_t *>(n_out);
+  DDHF_CUDA_TRY(c, cudaMemsetAsync(count, 0, sizeof(uint32_t), s));
+  k_box_root_init<<<blocks, 256, 0, s>>>(labels, bx, c->W, npx);
+  k_box_accum<<<blocks, 256, 0, s>>>(labels, bx, c->W, npx);
+  k_comp_collect<<<blocks, 256, 0, s>>>(labels, bx, npx, c->W, row0, out, cap, count);
   DDHF_CUDA_TRY(c, cudaGetLastError());
   return DDHF_OK;
 }

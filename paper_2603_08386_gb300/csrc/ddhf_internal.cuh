@@ -75,6 +75,7 @@ struct GridConst {
 
 struct Ctx {
   int W = 0, H = 0;
+  int row0 = 0;  // sensor row of row 0 (a row band of a larger sensor)
   int64_t npx = 0;
   ddhf_grid grid{};
   ddhf_params params{};
@@ -181,6 +182,8 @@ void set_bin_attributes();
 // ccl.cu
 ddhf_status launch_label(Ctx *c, const uint8_t *mask, int32_t *labels, uint64_t *n_fg,
                          cudaStream_t s);
+ddhf_status launch_components(Ctx *c, const int32_t *labels, int32_t row0, ddhf_component *out,
+                              int32_t cap, int32_t *n_out, cudaStream_t s);
 ddhf_status launch_boxes(Ctx *c, const int32_t *labels, ddhf_box *boxes, int32_t cap,
                          int32_t *n_boxes, cudaStream_t s);
 

@@ -67,6 +67,14 @@ class ddhf_tuning(ctypes.Structure):
                 ("fuse", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class ddhf_component(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in ("label", "x0", "y0", "x1", "y1", "n_px")]
+
+
+class ddhf_box(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in ("x0", "y0", "x1", "y1", "n_px")]
+
+
 # exported symbol -> (restype, argtypes)
 _VP, _I32, _I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
 SIGNATURES = {
@@ -96,6 +104,10 @@ SIGNATURES = {
     "ddhf_spectrum_median": (_I32, [_VP, _VP, _I64, _VP, _VP]),
     "ddhf_power_spectrum_noalloc": (_I32, [ctypes.POINTER(ddhf_grid), _VP, _VP, _I64, _VP, _I64,
                                            _VP, _I64, _VP]),
+    "ddhf_set_row_offset": (_I32, [_VP, _I32]),
+    "ddhf_components": (_I32, [_VP, _VP, _I32, _VP, _I32, _VP, _VP]),
+    "ddhf_merge_bands": (_I32, [_I32, _I32, _I32, _VP, _VP, _VP, _VP, ctypes.POINTER(ddhf_params),
+                                _VP, _I32, _VP]),
 }
 
 _lib = None
@@ -211,6 +223,37 @@ def ddhf_label(ctx, mask, labels, stream=None):
 def ddhf_boxes(ctx, labels, boxes, cap, n_boxes, stream=None):
     _check(load().ddhf_boxes(ctx, _ptr(labels), _ptr(boxes), int(cap), _ptr(n_boxes),
                              _stream(stream)), ctx)
+
+
+def ddhf_set_row_offset(ctx, row0):
+    _check(load().ddhf_set_row_offset(ctx, int(row0)), ctx)
+
+
+def ddhf_components(ctx, labels, row0, comps, cap, n_dev, stream=None):
+    """comps: int32 CUDA tensor [cap, 6] (label, x0, y0, x1, y1, n_px)."""
+    _check(load().ddhf_components(ctx, _ptr(labels), int(row0), _ptr(comps), int(cap),
+                                  _ptr(n_dev), _stream(stream)), ctx)
+
+
+def ddhf_merge_bands(W, H, band_row0, edge_labels, comps, comp_off, params, cap):
+    """Host call. band_row0 int32 [n+1], edge_labels int32 [n, 2, W] (band-local
+    labels), comps int32 [total, 6], comp_off int64 [n+1] (numpy arrays).
+    Returns (boxes int32 [min(total, cap), 5], total)."""
+    import numpy as np
+    n = len(band_row0) - 1
+    br = np.ascontiguousarray(band_row0, dtype=np.int32)
+    el = np.ascontiguousarray(edge_labels, dtype=np.int32)
+    cp = np.ascontiguousarray(comps, dtype=np.int32).reshape(-1, 6)
+    co = np.ascontiguousarray(comp_off, dtype=np.int64)
+    out = np.zeros((max(int(cap), 1), 5), dtype=np.int32)
+    nb = ctypes.c_int32(0)
+    st = load().ddhf_merge_bands(int(W), int(H), n, br.ctypes.data, el.ctypes.data,
+                                 cp.ctypes.data if cp.size else None, co.ctypes.data,
+                                 ctypes.byref(params), out.ctypes.data, int(cap),
+                                 ctypes.byref(nb))
+    if st not in (DDHF_OK, 3):  # CAPACITY: the first cap boxes are valid
+        _check(st)
+    return out[: min(nb.value, int(cap))].copy(), nb.value
 
 
 def ddhf_detect(ctx, x, y, t, p, n, t0, window_us, boxes, cap, n_boxes, mask_out=None,
