@@ -10,10 +10,10 @@ namespace {
 // Rows of P start every `ld` floats. The row is copied to shared memory with
 // all of a lane's loads in flight at once (16-byte loads when the rows are
 // 16-byte aligned), then scored by comb_warp.
-// 4 warps per block; the fast variant is held to 72 registers so that 7 blocks
-// fit on an SM with its 7.2 KB of shared memory per warp at 750 bins.
+// 4 warps per block; the fast variant is held to 64 registers so that 8 blocks
+// fit on an SM with its 6.9 KB of shared memory per warp at 750 bins.
 template <int NW>
-__global__ void __launch_bounds__(128, NW == 0 ? 7 : 1) k_comb(const float *__restrict__ P, int64_t ld, int64_t cap_px,
+__global__ void __launch_bounds__(128, NW == 0 ? 8 : 1) k_comb(const float *__restrict__ P, int64_t ld, int64_t cap_px,
                        const uint32_t *__restrict__ active, const uint64_t *__restrict__ counters,
                        CombConst cc, float *log_sf, float *snr, int32_t *f0, uint8_t *mask,
                        int warp_bytes, uint32_t *flags) {

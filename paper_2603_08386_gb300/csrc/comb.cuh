@@ -178,17 +178,24 @@ __device__ __forceinline__ int lin_bucket(float v, float scale) {
   return (int)fminf(__fmul_rn(v, scale), 1023.f);
 }
 
-// Smallest float v >= 0 with lin_bucket(v, scale) >= g, for 1 <= g <= 1023;
+// 512 linear buckets (the fast path's histogram).
+__device__ __forceinline__ int lin_bucket512(float v, float scale) {
+  return (int)fminf(__fmul_rn(v, scale), 511.f);
+}
+
+// Smallest float v >= 0 with lin_bucket512(v, scale) >= g, for 1 <= g <= 511;
 // -1 when the search does not settle (the caller then takes an exact path).
 __device__ __forceinline__ float bucket_low(int g, float scale) {
   float v = __fdiv_rn((float)g, scale);
   if (!(v > 0.f) || !(v < __int_as_float(0x7f800000))) return -1.f;
-  for (int it = 0; it < 8 && v > 0.f && lin_bucket(__uint_as_float(__float_as_uint(v) - 1u), scale) >= g; ++it)
+  for (int it = 0; it < 8 && v > 0.f &&
+                   lin_bucket512(__uint_as_float(__float_as_uint(v) - 1u), scale) >= g;
+       ++it)
     v = __uint_as_float(__float_as_uint(v) - 1u);
-  for (int it = 0; it < 8 && lin_bucket(v, scale) < g; ++it)
+  for (int it = 0; it < 8 && lin_bucket512(v, scale) < g; ++it)
     v = __uint_as_float(__float_as_uint(v) + 1u);
-  const bool ok = lin_bucket(v, scale) >= g &&
-                  (v == 0.f || lin_bucket(__uint_as_float(__float_as_uint(v) - 1u), scale) < g);
+  const bool ok = lin_bucket512(v, scale) >= g &&
+                  (v == 0.f || lin_bucket512(__uint_as_float(__float_as_uint(v) - 1u), scale) < g);
   return ok ? v : -1.f;
 }
 
@@ -465,7 +472,7 @@ __device__ __forceinline__ CombOut comb_warp_generic(const float *Pw, const Comb
 // Fast variant for N <= 1024 bins and a median band of at most 32 ranks.
 //
 // Same results as comb_warp_generic, bit for bit, with fewer instructions:
-//  * 1024 linear buckets over [0, 2 mean) are filled in the same pass as the
+//  * 512 linear buckets over [0, 2 mean) are filled in the same pass as the
 //    log sum of Eq. 7 (the Eq. 7 sums take 4-bin groups per lane);
 //  * the buckets holding ranks lo_r and hi_r bound the candidate set, which is
 //    extracted in one pass and sorted in registers as 32-bit keys (value bits
@@ -488,14 +495,14 @@ __device__ __forceinline__ CombOut comb_warp_generic(const float *Pw, const Comb
 // for the candidates that survive this test (or for all of them when more
 // than 64 survive).
 // Scratch layout (bytes from the scratch base, 16-byte aligned):
-//   [0, R)   R = max(5N, 4096): histogram u32[1024] during selection, then the
+//   [0, R)   R = max(5N, 2048): histogram u32[512] during selection, then the
 //            candidate values u32[64] and indices u16[64] (and the fallback's
 //            radix histogram), then the window maxima f32[N] and, from 4N,
 //            one code byte per bin: its band position 0..31, 32 below the
 //            band, 64 above it
 //   [R, R + 128)  surviving candidates u16[64]
 struct CombFast {
-  __host__ __device__ static int rec_bytes(int N) { return 5 * N > 4096 ? 5 * N : 4096; }
+  __host__ __device__ static int rec_bytes(int N) { return 5 * N > 2048 ? 5 * N : 2048; }
   __host__ __device__ static int list_off(int N) { return (rec_bytes(N) + 15) & ~15; }
   __host__ __device__ static int bytes(int N) { return list_off(N) + 128; }
   static constexpr int kMaxN = 1024;
@@ -607,7 +614,7 @@ __device__ __forceinline__ CombOut comb_warp_fast(const float *Pw, const CombCon
   // ---- Eq. 7 sums (fixed order: 4-bin groups lane-strided, then a
   // butterfly) and the histogram
 #pragma unroll
-  for (int q = 0; q < 8; ++q)
+  for (int q = 0; q < 4; ++q)
     reinterpret_cast<uint4 *>(hist)[q * 32 + lane] = make_uint4(0u, 0u, 0u, 0u);
   // full 4-bin groups, then the (at most 3) tail bins in the lane owning
   // group N / 4, in bin order
@@ -624,7 +631,7 @@ __device__ __forceinline__ CombOut comb_warp_fast(const float *Pw, const CombCon
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) sum = __fadd_rn(sum, __shfl_xor_sync(0xffffffffu, sum, o));
   const float fN = (float)N;
-  const float scale = __fdiv_rn(512.f, __fdiv_rn(sum, fN));
+  const float scale = __fdiv_rn(256.f, __fdiv_rn(sum, fN));
   __syncwarp();
   float slog = 0.f;
   for (int q = lane; q < nfull; q += 32) {
@@ -633,16 +640,16 @@ __device__ __forceinline__ CombOut comb_warp_fast(const float *Pw, const CombCon
     slog = __fadd_rn(slog, ln_normal(fmaxf(v.y, 1e-30f)));
     slog = __fadd_rn(slog, ln_normal(fmaxf(v.z, 1e-30f)));
     slog = __fadd_rn(slog, ln_normal(fmaxf(v.w, 1e-30f)));
-    atomicAdd(&hist[lin_bucket(v.x, scale)], 1u);
-    atomicAdd(&hist[lin_bucket(v.y, scale)], 1u);
-    atomicAdd(&hist[lin_bucket(v.z, scale)], 1u);
-    atomicAdd(&hist[lin_bucket(v.w, scale)], 1u);
+    atomicAdd(&hist[lin_bucket512(v.x, scale)], 1u);
+    atomicAdd(&hist[lin_bucket512(v.y, scale)], 1u);
+    atomicAdd(&hist[lin_bucket512(v.z, scale)], 1u);
+    atomicAdd(&hist[lin_bucket512(v.w, scale)], 1u);
   }
   if (lane == tail_lane) {
     for (int j = jt; j < N; ++j) {
       const float v = Pw[j];
       slog = __fadd_rn(slog, ln_normal(fmaxf(v, 1e-30f)));
-      atomicAdd(&hist[lin_bucket(v, scale)], 1u);
+      atomicAdd(&hist[lin_bucket512(v, scale)], 1u);
     }
   }
 #pragma unroll
@@ -651,14 +658,14 @@ __device__ __forceinline__ CombOut comb_warp_fast(const float *Pw, const CombCon
   if (!(out.log_sf <= cc.ln_tau_sf) || cc.w_hi < cc.w_lo) return out;
   __syncwarp();
 
-  // ---- buckets of ranks lo_r and hi_r; lane l owns buckets [32 l, 32 l + 32)
+  // ---- buckets of ranks lo_r and hi_r; lane l owns buckets [16 l, 16 l + 16)
   const int lo_r = cc.lo_r, bw = cc.bw, hi_r = cc.lo_r + cc.bw - 1;
   uint32_t lsum = 0;
   {
-    const uint4 *h4 = reinterpret_cast<const uint4 *>(hist) + lane * 8;
+    const uint4 *h4 = reinterpret_cast<const uint4 *>(hist) + lane * 4;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const uint4 t = h4[(q + lane) & 7];  // rotated: no bank conflicts
+    for (int q = 0; q < 4; ++q) {
+      const uint4 t = h4[(q + (lane >> 1)) & 3];  // rotated: no bank conflicts
       lsum += t.x + t.y + t.z + t.w;
     }
   }
@@ -676,7 +683,7 @@ __device__ __forceinline__ CombOut comb_warp_fast(const float *Pw, const CombCon
       bad = true;
     }
     const uint32_t base = __shfl_sync(0xffffffffu, lex, src);
-    const uint32_t h = hist[src * 32 + lane];
+    const uint32_t h = lane < 16 ? hist[src * 16 + lane] : 0u;
     uint32_t t2;
     const uint32_t ex = warp_excl_scan<uint32_t>(h, t2) + base;
     int s2 = __ffs(__ballot_sync(0xffffffffu, R >= ex && R < ex + h)) - 1;
@@ -684,7 +691,7 @@ __device__ __forceinline__ CombOut comb_warp_fast(const float *Pw, const CombCon
       s2 = 0;
       bad = true;
     }
-    gsel[t] = src * 32 + s2;
+    gsel[t] = src * 16 + s2;
     gbelow[t] = __shfl_sync(0xffffffffu, ex, s2);
     gcount[t] = __shfl_sync(0xffffffffu, h, s2);
   }
@@ -704,7 +711,7 @@ __device__ __forceinline__ CombOut comb_warp_fast(const float *Pw, const CombCon
     // candidates are the bins with vlo <= P < vhi, the value bounds of buckets
     // gsel[0] .. gsel[1] (exact: checked against the bucket function)
     const float vlo = gsel[0] == 0 ? 0.f : bucket_low(gsel[0], scale);
-    const float vhi = gsel[1] >= 1023 ? __int_as_float(0x7f800000) : bucket_low(gsel[1] + 1, scale);
+    const float vhi = gsel[1] >= 511 ? __int_as_float(0x7f800000) : bucket_low(gsel[1] + 1, scale);
     if (vlo < 0.f || vhi < 0.f) slow = true;
     uint32_t run = 0;
     for (int q0 = 0; q0 < ng; q0 += 32) {
