@@ -54,6 +54,13 @@ def _gen_window(args):
     return sc.x, sc.y, sc.t, sc.p, sc.t0, sc.window_us, sc.n
 
 
+def _gen_c4(b):
+    # window b of the soft-comb batch (640x480, 40 ms, 750 bins), as config4_batch makes it
+    sc = synth.config2(1004 * 1000 + b, W=640, H=480, window_us=40_000,
+                       grid=synth.hz_grid(0, 2, 750))
+    return sc.x, sc.y, sc.t, sc.p, sc.t0, sc.window_us, sc.n
+
+
 def rank_seed(rank: int) -> int:
     """Seed of a rank's batch: ranks are independent replicas (weak scaling)."""
     return 1003 + 1000 * rank
@@ -83,11 +90,30 @@ def generate(rank: int, procs: int, n_windows: int = N_STREAMS * N_WINDOWS, W: i
         return pool.map(_gen_window, jobs, chunksize=1)
 
 
-def terms_of(win, W, H, n_bins, n_min=6):
+def _counts(win, W, H):
     x, y, t, p, t0, wus, n = win
     ok = (x >= 0) & (x < W) & (y >= 0) & (y < H) & (t >= t0) & (t < t0 + wus) & (p != 0)
-    cnt = np.bincount(y[ok].astype(np.int64) * W + x[ok], minlength=W * H)
+    return np.bincount(y[ok].astype(np.int64) * W + x[ok], minlength=W * H)
+
+
+def terms_of(win, W, H, n_bins, n_min=6):
+    cnt = _counts(win, W, H)
     return int(cnt[cnt >= n_min].sum()) * n_bins
+
+
+def active_of(win, W, H, n_min=6):
+    return int((_counts(win, W, H) >= n_min).sum())
+
+
+def measured_peaks():
+    """Measured peaks of this GPU pool, else the recipe's fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return dict(hbm_gbs=float(d["hbm_gbs"]), source="measured")
+    except (OSError, ValueError, KeyError):
+        return dict(hbm_gbs=6800.0, source="fallback")
 
 
 class Clocks:
@@ -208,6 +234,8 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default tuning)")
     ap.add_argument("--procs", type=int, default=int(os.environ.get("DDHF_GEN_PROCS", "16")))
     ap.add_argument("--no-latency", action="store_true", help="skip the one-window latency")
+    ap.add_argument("--no-softcomb", action="store_true", help="skip the soft-comb timing")
+    ap.add_argument("--softcomb-windows", type=int, default=2)
     ap.add_argument("--latency-replays", type=int, default=100)
     ap.add_argument("--sensor", default="1280x720",
                     help="WxH of the synthetic sensor (smaller sizes for profiling captures)")
@@ -221,6 +249,11 @@ def main():
     W, H = (int(v) for v in args.sensor.lower().split("x"))
     # inputs are generated before any CUDA call (spawned workers)
     wins = generate(rank, max(1, args.procs // max(1, world)), args.windows, W, H)
+    c4 = []
+    if not args.no_softcomb and args.softcomb_windows > 0:
+        with mp.get_context("spawn").Pool(processes=max(1, min(args.procs,
+                                                                  args.softcomb_windows))) as pool:
+            c4 = pool.map(_gen_c4, range(args.softcomb_windows))
 
     import torch
     from paper_2603_08386_gb300 import build, ddhf
@@ -346,6 +379,57 @@ def main():
                    events=int(wins[0][6]), replays=len(lt), median_ms=float(q50),
                    iqr_ms=float(q75 - q25), p95_ms=float(q95), min_ms=float(lt.min()))
         lc.close()
+    # ------------------------------------------------------------ soft comb and its adjoint
+    # every active pixel of each 640x480 window: S and dS/d(f0, w, sigma) for
+    # 6 harmonics x (2Q+1) = 42 evaluation frequencies per pixel
+    softc = None
+    if c4:
+        Q, delta, n_h = 3, 2.0, 6
+        fw_ms, bw_ms, terms_sc, pix_sc = [], [], 0, 0
+        gen = torch.Generator(device="cuda").manual_seed(1004)
+        for (x4, y4, t4, p4, t04, w4, n4) in c4:
+            cc = ddhf.Context(640, 480, grid, max_events=n4)
+            d4 = [torch.from_numpy(a).cuda() for a in (x4, y4, t4, p4)]
+            cc.bin_events(*d4, t04, w4)
+            csr = cc.csr()
+            pix = csr["active"]
+            na = pix.numel()
+            offs = csr["offsets"].long()
+            cnt = int((offs[pix.long() + 1] - offs[pix.long()]).sum().item())
+            f0 = 50.0 + 150.0 * torch.rand(na, device="cuda", generator=gen)
+            wv = torch.ones(n_h, device="cuda")
+            sg = torch.full((n_h,), 2.0, device="cuda")
+            Bv = torch.ones(na, device="cuda")
+            Sv = torch.empty(na, device="cuda")
+            gS = torch.ones(na, device="cuda")
+            gf, gw, gsg = torch.empty(na, device="cuda"), torch.empty(n_h, device="cuda"), \
+                torch.empty(n_h, device="cuda")
+            fwd = lambda: ddhf.ddhf_softcomb(cc.h, pix, f0, n_h, Q, delta, w4 / 2, wv, sg, Bv, S=Sv)
+            bwd = lambda: ddhf.ddhf_softcomb(cc.h, pix, f0, n_h, Q, delta, w4 / 2, wv, sg, Bv,
+                                             grad_S=gS, grad_f0=gf, grad_w=gw, grad_sigma=gsg)
+            for fn, acc in ((fwd, fw_ms), (bwd, bw_ms)):
+                fn()
+                torch.cuda.synchronize()
+                a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a0.record()
+                for _ in range(5):
+                    fn()
+                a1.record()
+                torch.cuda.synchronize()
+                acc.append(a0.elapsed_time(a1) / 5)
+            cc.stats()
+            cc.close()
+            terms_sc += cnt * n_h * (2 * Q + 1)
+            pix_sc += na
+        nwc = len(c4)
+        softc = dict(workload=f"{nwc} windows of 640x480, 40 ms (C2 density), 750-bin grid; "
+                              "all active pixels; 6 harmonics, Q=3, delta 2 Hz",
+                     pixels=pix_sc, terms=terms_sc,
+                     fwd_ms_per_window=statistics.mean(fw_ms),
+                     bwd_ms_per_window=statistics.mean(bw_ms),
+                     fwd_terms_per_s=terms_sc / (sum(fw_ms) * 1e-3),
+                     bwd_terms_per_s=terms_sc / (sum(bw_ms) * 1e-3),
+                     unit="event x evaluation-frequency terms/s")
     # ------------------------------------------------------------ plain per-pixel pipeline
     plain = None
     if not args.no_plain:
@@ -396,6 +480,29 @@ def main():
     else:
         ndft_ms, kern = statistics.mean(spec_ms), "blocked NDFT spectrum kernel (k_blocked<TB,1,0>)"
     achieved = OPS_PER_TERM * terms_step / (ndft_ms * 1e-3) / 1e12
+    roof_ndft = dict(bound="alu", achieved=achieved, peak=peak, unit="Tops/s",
+                     frac=achieved / peak, traffic=None, kernel=kern,
+                     kernel_ms_per_step=ndft_ms, share_of_step=ndft_ms / ms_step,
+                     peak_source="derived: 152 SMs x 128 FP32 lanes x 2070 MHz",
+                     ops="3 FP32 FMA-pipe lane-ops per term (three-multiplication complex "
+                         "product)")
+    roof_comb = None
+    if not fused_mode:
+        pk = measured_peaks()
+        n_act = sum(active_of(w, W, H) for w in wins)
+        # algorithmic bytes: read every active pixel's spectrum row, write its
+        # four results (4 + 4 + 4 + 1 B), clear the window's mask
+        comb_bytes = n_act * (nb * 4 + 13) + nwin * W * H
+        comb_t = statistics.mean(comb_ms)
+        ach = comb_bytes / (comb_t * 1e-3) / 1e9
+        roof_comb = dict(bound="hbm", achieved=ach, peak=pk["hbm_gbs"], unit="GB/s",
+                         frac=ach / pk["hbm_gbs"], traffic=None,
+                         kernel="SF + comb kernel (k_comb<0>)", kernel_ms_per_step=comb_t,
+                         share_of_step=comb_t / ms_step, peak_source=pk["source"],
+                         bytes_per_step=comb_bytes,
+                         note="far below the HBM bound: instruction-issue and latency bound "
+                              "(selection, window maxima, per-candidate medians)")
+    dominant = roof_comb if roof_comb and roof_comb["kernel_ms_per_step"] > ndft_ms else roof_ndft
     metric = METRIC if (W, H) == (1280, 720) else METRIC.replace("1280x720", f"{W}x{H}")
     line = dict(
         metric=metric, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
@@ -413,14 +520,12 @@ def main():
                     l2="inputs 8.3 GB per step, larger than L2; no flush",
                     tuning=dict(tuning, how=tune_note),
                     parallelism=f"replicas x{world}"),
-        roofline=dict(bound="alu", achieved=achieved, peak=peak, unit="Tops/s",
-                      frac=achieved / peak, traffic=None, kernel=kern,
-                      kernel_ms_per_step=ndft_ms, share_of_step=ndft_ms / ms_step,
-                      ops="3 FP32 FMA-pipe lane-ops per term (three-multiplication complex "
-                          "product); peak = 152 SMs x 128 FP32 lanes x 2070 MHz",
-                      comb_kernel_ms_per_step=None if fused_mode else statistics.mean(comb_ms)),
+        roofline=dominant,
+        roofline_ndft=roof_ndft,
+        roofline_comb=roof_comb,
         e2e=e2e,
         window_latency=lat,
+        softcomb=softc,
         gpu_launches=int(graph_kernels) * args.steps,
         clocks=clk,
         plain=plain,
