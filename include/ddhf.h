@@ -289,9 +289,11 @@ ddhf_status ddhf_stage_times(ddhf_ctx *ctx, float *out_ms);
  *   G_hq = exp(-(q delta)^2 / (2 sigma_h^2)),  Z_h = sum_q G_hq
  *   S[a] = sum_h w_h (sum_q G_hq P_a(f_hq) / Z_h) / B[a]
  * where P_a(f) = |sum_k p_k exp(-2 pi i f (tau_k - tau_c_us) 1e-6)|^2 is Eq. 6
- * at a real frequency (exact integer-mHz phase plus a sub-mHz remainder) and
- * B[a] > 0 a constant background (e.g. ddhf_spectrum_median of the grid
- * spectrum). w, sigma: [n_h] device floats.
+ * at a real frequency (exact integer-mHz phase plus a sub-mHz remainder; f0
+ * and delta_hz are rounded to 1 micro-Hz, tau_c_us to 0.5 us, which changes
+ * neither P nor dP/df) and B[a] > 0 a constant background (e.g.
+ * ddhf_spectrum_median of the grid spectrum). w, sigma: [n_h] device floats.
+ * Requires 1e-6 <= delta_hz < 1e6 and 0 <= tau_c_us < 2^20.
  * Forward (grad_S == NULL): writes S[n_px].
  * Backward (grad_S != NULL, S ignored): with g = grad_S,
  *   grad_f0[a] = g[a] dS_a/df0,  grad_w[h] = sum_a g[a] dS_a/dw_h,

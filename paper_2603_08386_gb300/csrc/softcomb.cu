@@ -10,11 +10,13 @@
 // dP/df = 2 Re(conj(F) D), D = sum_k (-2 pi i (tau_k - tau_c)) p_k exp(...).
 //
 // One warp per pixel; lanes hold events (32 per chunk). For each harmonic h
-// the phasor of event k at q = -Q is seeded exactly: the frequency is split
-// into an integer number of mHz (exact residue of a * tau mod 1e9, as in the
-// grid NDFT) plus a sub-mHz remainder and the constant window-centre phase,
-// both evaluated in FP64 once per (pixel, h); the next q values follow by
-// rotation with e^{-2 pi i delta (tau - tau_c)}. F and D for the 2Q+1
+// the phasor of event k at q = -Q is seeded exactly: the frequency, an
+// integer number of micro-Hz (f0 and delta rounded to 1 uHz), is split into
+// integer mHz (exact residue of a * tau mod 1e9, as in the grid NDFT) plus a
+// sub-mHz remainder, and the constant window-centre phase is reduced exactly
+// in integers (tau_c in half-microseconds); no FP64 arithmetic runs per
+// harmonic or per event. The next q values follow by rotation with
+// e^{-2 pi i delta (tau - tau_c)}. F and D for the 2Q+1
 // frequencies are accumulated per lane and reduced over the warp in a fixed
 // order. Per-pixel gradient contributions to w and sigma are written to a
 // workspace and summed over pixels by a fixed-order reduction, so every
@@ -39,8 +41,9 @@ struct SoftArgs {
   const float *sigma;
   const float *B;
   int n_h, Q;
-  double delta;            // Hz
-  double tau_c;            // us, relative to the window start
+  int64_t delta_uhz;       // evaluation step in micro-Hz
+  float delta_hz;          // the same step in Hz
+  int64_t tc2;             // 2 tau_c in half-microseconds (tau_c relative to the window start)
   float *S;                // forward output [n_px]
   const float *gS;         // backward input [n_px]
   float *g_f0;             // backward output [n_px]
@@ -60,19 +63,29 @@ __global__ void __launch_bounds__(256) k_softcomb(SoftArgs A) {
     const uint32_t key = A.pixels[a];
     const uint32_t o0 = A.offsets[key];
     const int cnt = (int)(A.offsets[key + 1] - o0);
-    const double f0 = (double)A.f0[a];
+    // f0 in integer micro-Hz: every frequency h f0 + q delta is then an exact
+    // integer number of micro-Hz, split into integer mHz (exact residue
+    // a tau mod 1e9, as in the grid NDFT) plus a remainder below 1 mHz
+    const int64_t f0u = __double2ll_rn((double)A.f0[a] * 1e6);
     const float Bv = A.B[a];
     float S = 0.f, g0 = 0.f;
     for (int h = 1; h <= A.n_h; ++h) {
-      // frequency of q = -Q, split into integer mHz + remainder
-      const double fb = (double)h * f0 - (double)A.Q * A.delta;
-      const double fmhz = floor(fb * 1000.0);
-      const int64_t ai_s = (int64_t)fmhz % (int64_t)D9;               // residue, any sign
-      const uint64_t ai = (uint64_t)(ai_s < 0 ? ai_s + (int64_t)D9 : ai_s);
-      const float fr = (float)(fb - fmhz * 1e-3);                  // Hz, in [0, 1e-3)
-      double cf = fb * A.tau_c * 1e-6;
-      cf -= floor(cf);                                              // cycles, constant phase
-      const float cff = (float)cf;
+      const int64_t fbu = (int64_t)h * f0u - (int64_t)A.Q * A.delta_uhz;  // q = -Q
+      int64_t fm = fbu / 1000, rem = fbu - fm * 1000;
+      if (rem < 0) {
+        rem += 1000;
+        fm -= 1;
+      }
+      const uint64_t am = mod_barrett((uint64_t)(fm < 0 ? -fm : fm), D9, A.barrett);
+      const uint64_t ai = (fm < 0 && am != 0) ? D9 - am : am;        // fm mod 1e9
+      const float fr = __fmul_rn((float)rem, 1e-6f);                 // Hz, in [0, 1e-3)
+      // constant phase f tau_c in cycles: (fbu * tc2 / 2e12) mod 1, exactly in
+      // integers (fbu mod 2e12 < 2^41, tc2 < 2^21)
+      const int64_t P2 = 2000000000000ll;
+      int64_t fmod2 = fbu % P2;
+      if (fmod2 < 0) fmod2 += P2;
+      const int64_t cm = (int64_t)(((uint64_t)fmod2 * (uint64_t)A.tc2) % (uint64_t)P2);
+      const float cff = __fmul_rn((float)cm, 5e-13f);
       float Fr[2 * kSoftMaxQ + 1], Fi[2 * kSoftMaxQ + 1];
       float Dr[2 * kSoftMaxQ + 1], Di[2 * kSoftMaxQ + 1];
 #pragma unroll
@@ -91,9 +104,9 @@ __global__ void __launch_bounds__(256) k_softcomb(SoftArgs A) {
           float sn, cs;
           sincospif(2.f * x, &sn, &cs);
           float zr = sg * cs, zi = -sg * sn;
-          const float tt = (float)(((double)tau - A.tau_c) * 1e-6);  // seconds
+          const float tt = __fmul_rn((float)((int64_t)(2 * tau) - A.tc2), 0.5e-6f);  // s
           float ss, sc;
-          sincospif(2.f * (float)(A.delta * (((double)tau - A.tau_c) * 1e-6)), &ss, &sc);
+          sincospif(2.f * __fmul_rn(A.delta_hz, tt), &ss, &sc);
           const float ur = sc, ui = -ss;
           const float wtt = kTwoPi * tt;
 #pragma unroll
@@ -133,7 +146,7 @@ __global__ void __launch_bounds__(256) k_softcomb(SoftArgs A) {
 #pragma unroll
       for (int q = 0; q < 2 * kSoftMaxQ + 1; ++q) {
         if (q < nq) {
-          const float qd = (float)((double)(q - A.Q) * A.delta);
+          const float qd = __fmul_rn((float)(q - A.Q), A.delta_hz);
           const float G = expf(-(qd * qd) / (2.f * sgm * sgm));
           const float P = Fr[q] * Fr[q] + Fi[q] * Fi[q];
           Z += G;
@@ -270,7 +283,9 @@ extern "C" ddhf_status ddhf_softcomb(ddhf_ctx *h, int64_t n_px, const uint32_t *
     return DDHF_ERR_STATE;
   }
   if (n_px < 0 || n_px > c->npx || n_h < 1 || n_h > kSoftMaxH || Q < 0 || Q > kSoftMaxQ ||
-      !(delta_hz > 0.0) || (n_px > 0 && (!pixels || !f0 || !w || !sigma || !B))) {
+      !(delta_hz >= 1e-6) || !(delta_hz < 1e6) || !(tau_c_us >= 0.0) ||
+      !(tau_c_us < (double)(1 << 20)) ||
+      (n_px > 0 && (!pixels || !f0 || !w || !sigma || !B))) {
     c->last_error = "softcomb: bad arguments";
     return DDHF_ERR_INVALID_ARG;
   }
@@ -297,8 +312,9 @@ extern "C" ddhf_status ddhf_softcomb(ddhf_ctx *h, int64_t n_px, const uint32_t *
   A.B = B;
   A.n_h = n_h;
   A.Q = Q;
-  A.delta = delta_hz;
-  A.tau_c = tau_c_us;
+  A.delta_uhz = llround(delta_hz * 1e6);
+  A.delta_hz = (float)delta_hz;
+  A.tc2 = llround(2.0 * tau_c_us);
   A.S = S;
   A.gS = grad_S;
   A.g_f0 = grad_f0;
