@@ -79,23 +79,80 @@ __global__ void __launch_bounds__(kBinThreads) k_hist(RawIn raw, const uint32_t 
   for (int d = threadIdx.x; d < nb; d += blockDim.x) hist[(int64_t)d * nchunks + chunk] = sh[d];
 }
 
+// Exclusive scan in place of a[0..n) (n <= 2048) by one block of kBinThreads
+// threads; returns the total. Uses `tmp` (kBinThreads / 32 words).
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t *a, int n, uint32_t *tmp) {
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int per = (n + kBinThreads - 1) / kBinThreads;  // <= 8
+  uint32_t v[8], s = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int j = t * per + i;
+    v[i] = (i < per && j < n) ? a[j] : 0u;
+    s += v[i];
+  }
+  uint32_t inc = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t u = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += u;
+  }
+  if (lane == 31) tmp[warp] = inc;
+  __syncthreads();
+  uint32_t wpre = 0, tot = 0;
+  for (int w = 0; w < kBinThreads / 32; ++w) {
+    if (w < warp) wpre += tmp[w];
+    tot += tmp[w];
+  }
+  uint32_t run = wpre + inc - s;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int j = t * per + i;
+    if (i < per && j < n) {
+      a[j] = run;
+      run += v[i];
+    }
+  }
+  __syncthreads();
+  return tot;
+}
+
+// Stable scatter of one chunk: every kept element gets its rank among equal
+// digits earlier in the chunk (warp match + per-warp counters, as in the
+// histogram), is staged in shared memory in the chunk's digit order, and the
+// staged chunk is written out so that each digit's elements go to consecutive
+// addresses (coalesced runs) starting at that (digit, chunk)'s offset from the
+// scanned table. n_total: kept elements of the whole array (the table's sum).
 template <bool RAW>
 __global__ void __launch_bounds__(kBinThreads) k_scatter(
     RawIn raw, const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin,
-    const uint32_t *__restrict__ n_dev, uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
-    const uint32_t *__restrict__ hscan, int64_t nchunks, int shift, int nb) {
+    const uint32_t *__restrict__ n_total, uint32_t *__restrict__ kout,
+    uint32_t *__restrict__ vout, const uint32_t *__restrict__ hscan, int64_t nchunks, int shift,
+    int nb) {
   extern __shared__ uint32_t sm[];
   const int stride = nb + 1;
-  uint32_t *wcnt = sm;                       // [8][nb + 1] per-warp counts this round
-  uint32_t *run = wcnt + 8 * stride;         // [nb + 1] counts of earlier rounds
-  uint32_t *base = run + stride;             // [nb] global offset of (digit, chunk)
-  const int64_t n = RAW ? raw.n : (int64_t)*n_dev;
+  uint32_t *wcnt = sm;                 // [8][nb + 1] per-warp counts this round
+  uint32_t *run = wcnt + 8 * stride;   // [nb + 1] counts of earlier rounds
+  uint32_t *base = run + stride;       // [nb] global offset of (digit, chunk)
+  uint32_t *lst = base + nb;           // [nb] start of each digit in the staged chunk
+  uint32_t *sk = lst + nb;             // [kBinChunk] staged keys
+  uint32_t *sv = sk + kBinChunk;       // [kBinChunk] staged values
+  __shared__ uint32_t scan_tmp[kBinThreads / 32];
+  const int64_t n = RAW ? raw.n : (int64_t)*n_total;
   const int64_t chunk = blockIdx.x;
   const int64_t c0 = chunk * kBinChunk;
   if (c0 >= n) return;
+  const int64_t ncells = (int64_t)nb * nchunks;
+  const uint32_t total = *n_total;
   for (int i = threadIdx.x; i < 9 * stride; i += blockDim.x) sm[i] = 0;
-  for (int d = threadIdx.x; d < nb; d += blockDim.x) base[d] = hscan[(int64_t)d * nchunks + chunk];
+  for (int d = threadIdx.x; d < nb; d += blockDim.x) {
+    const int64_t cell = (int64_t)d * nchunks + chunk;
+    const uint32_t b = hscan[cell];
+    base[d] = b;
+    lst[d] = (cell + 1 < ncells ? hscan[cell + 1] : total) - b;  // this chunk's count of d
+  }
   __syncthreads();
+  const uint32_t m = block_excl_scan(lst, nb, scan_tmp);  // kept elements of the chunk
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1;
   uint32_t *my = wcnt + warp * stride;
@@ -133,9 +190,11 @@ __global__ void __launch_bounds__(kBinThreads) k_scatter(
       if (d < (uint32_t)nb) {
         uint32_t pre = run[d] + rk[i];
         for (int w2 = 0; w2 < warp; ++w2) pre += wcnt[w2 * stride + d];
-        uint32_t dest = base[d] + pre;
-        kout[dest] = kk[i];
-        vout[dest] = vv[i];
+        const uint32_t slot = lst[d] + pre;
+        if (slot < (uint32_t)kBinChunk) {
+          sk[slot] = kk[i];
+          sv[slot] = vv[i];
+        }
       }
     }
     __syncthreads();
@@ -149,6 +208,14 @@ __global__ void __launch_bounds__(kBinThreads) k_scatter(
       run[d] += s;
     }
     __syncthreads();
+  }
+  // staged chunk out: consecutive slots of one digit go to consecutive addresses
+  for (uint32_t sl = threadIdx.x; sl < m && sl < (uint32_t)kBinChunk; sl += blockDim.x) {
+    const uint32_t key = sk[sl];
+    const uint32_t d = (key >> shift) & (uint32_t)(nb - 1);
+    const uint32_t dest = base[d] + (sl - lst[d]);
+    kout[dest] = key;
+    vout[dest] = sv[sl];
   }
 }
 
@@ -328,7 +395,7 @@ ddhf_status bin_window(Ctx *c, int slot_i, const int16_t *x, const int16_t *y, c
       uint32_t *vo = last ? sl.ev : vbuf[pass & 1];
       const uint32_t *ki = pass ? kbuf[(pass - 1) & 1] : nullptr;
       const uint32_t *vi = pass ? vbuf[(pass - 1) & 1] : nullptr;
-      const size_t smem = (size_t)(9 * (nb + 1) + nb) * sizeof(uint32_t);
+      const size_t smem = (size_t)(9 * (nb + 1) + 2 * nb + 2 * kBinChunk) * sizeof(uint32_t);
       if (pass == 0) {
         k_hist<true><<<(unsigned)nch, kBinThreads, 0, s>>>(raw, nullptr, nullptr, c->hist, nch,
                                                            shift, nb);
@@ -341,7 +408,7 @@ ddhf_status bin_window(Ctx *c, int slot_i, const int16_t *x, const int16_t *y, c
       DDHF_CUDA_TRY(c, scan_rec<uint32_t>(c->hist, c->hist, (int64_t)nb * nch, c->scan_part,
                                           pass == 0 ? ntot : nullptr, s));
       if (pass == 0) {
-        k_scatter<true><<<(unsigned)nch, kBinThreads, smem, s>>>(raw, nullptr, nullptr, nullptr, ko,
+        k_scatter<true><<<(unsigned)nch, kBinThreads, smem, s>>>(raw, nullptr, nullptr, ntot, ko,
                                                                  vo, c->hist, nch, shift, nb);
       } else {
         k_scatter<false><<<(unsigned)nch, kBinThreads, smem, s>>>(raw, ki, vi, ntot, ko, vo,
@@ -373,7 +440,8 @@ ddhf_status bin_window(Ctx *c, int slot_i, const int16_t *x, const int16_t *y, c
 }
 
 void set_bin_attributes() {
-  const int smem = (9 * ((1 << kMaxDigitBits) + 1) + (1 << kMaxDigitBits)) * sizeof(uint32_t);
+  const int smem =
+      (9 * ((1 << kMaxDigitBits) + 1) + 2 * (1 << kMaxDigitBits) + 2 * kBinChunk) * sizeof(uint32_t);
   cudaFuncSetAttribute(k_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   cudaFuncSetAttribute(k_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
