@@ -10,7 +10,8 @@
 // offset + (its rank among equal digits earlier in the chunk). The in-chunk
 // rank is computed warp by warp with __match_any_sync and per-warp digit
 // counters in shared memory, so element order inside a digit is input order
-// and every pass is stable; no block waits on another block. The first pass
+// and every pass is stable; the chunk is staged in shared memory in digit
+// order and written out in contiguous runs; no block waits on another block. The first pass
 // reads the raw (x, y, t, p) arrays directly and packs each kept event into
 // one 32-bit word: tau = t - t0 in bits 0-30, bit 31 set for polarity -1.
 // Per-pixel counts come from segment boundaries of the sorted keys, and one
@@ -59,7 +60,6 @@ __global__ void __launch_bounds__(kBinThreads) k_hist(RawIn raw, const uint32_t 
   for (int d = threadIdx.x; d < nb; d += blockDim.x) sh[d] = 0;
   __syncthreads();
   const int64_t c1 = min(n, c0 + (int64_t)kBinChunk);
-  const uint32_t lane = threadIdx.x & 31;
   for (int64_t base = c0; base < c1; base += blockDim.x) {
     int64_t e = base + threadIdx.x;
     uint32_t d = (uint32_t)nb;  // sentinel: not counted
@@ -71,9 +71,7 @@ __global__ void __launch_bounds__(kBinThreads) k_hist(RawIn raw, const uint32_t 
         d = (kin[e] >> shift) & (uint32_t)(nb - 1);
       }
     }
-    uint32_t peers = __match_any_sync(0xffffffffu, d);
-    if (d < (uint32_t)nb && __popc(peers & ((1u << lane) - 1)) == 0)
-      atomicAdd(&sh[d], (uint32_t)__popc(peers));
+    if (d < (uint32_t)nb) atomicAdd(&sh[d], 1u);
   }
   __syncthreads();
   for (int d = threadIdx.x; d < nb; d += blockDim.x) hist[(int64_t)d * nchunks + chunk] = sh[d];
