@@ -146,13 +146,39 @@ __device__ __forceinline__ uint64_t mod_barrett(uint64_t x, uint64_t D, uint64_t
   return r;
 }
 
-// e^{-2 pi i r / D} for an exact residue 0 <= r < D, via sincospi on the
+// sin(pi x) and cos(pi x) for |x| <= 1: x = y + q/2 with q = rint(2x) (the
+// subtraction is exact), then sin(pi y) = y P(y^2) and cos(pi y) = 1 + y^2 C(y^2)
+// on |y| <= 1/4 with polynomials fitted by weighted least squares (relative
+// error, FP64) and rounded to FP32; the quadrant q mod 4 swaps and negates.
+// Error within 2 ulp of the exact values (checked against sincospif).
+__device__ __forceinline__ void sincospi_reduced(float x, float &s, float &c) {
+  const float q = rintf(__fmul_rn(2.f, x));
+  const float y = __fmaf_rn(-0.5f, q, x);
+  const float t = __fmul_rn(y, y);
+  float p = 0.0810556039f;
+  p = __fmaf_rn(p, t, -0.599208117f);
+  p = __fmaf_rn(p, t, 2.55016279f);
+  p = __fmaf_rn(p, t, -5.16771269f);
+  p = __fmaf_rn(p, t, 3.14159274f);
+  const float sy = __fmul_rn(y, p);
+  float k = 0.231556028f;
+  k = __fmaf_rn(k, t, -1.33507168f);
+  k = __fmaf_rn(k, t, 4.05870819f);
+  k = __fmaf_rn(k, t, -4.93480206f);
+  const float cy = __fmaf_rn(k, t, 1.f);
+  const int iq = (int)q & 3;  // 0: (sy, cy), 1: (cy, -sy), 2: (-sy, -cy), 3: (-cy, sy)
+  const float s0 = (iq & 1) ? cy : sy, c0 = (iq & 1) ? sy : cy;
+  s = (iq & 2) ? -s0 : s0;
+  c = (iq == 1 || iq == 2) ? -c0 : c0;
+}
+
+// e^{-2 pi i r / D} for an exact residue 0 <= r < D, via sin/cos(pi x) of the
 // half-open turn x = 2r/D folded to [-1, 1].
 __device__ __forceinline__ float2 phasor_of_residue(uint64_t r, float two_over_denom) {
   float x = __fmul_rn((float)r, two_over_denom);
   if (x > 1.0f) x = __fsub_rn(x, 2.0f);
   float s, c;
-  sincospif(x, &s, &c);
+  sincospi_reduced(x, s, c);
   return make_float2(c, -s);
 }
 

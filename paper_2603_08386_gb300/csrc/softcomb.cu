@@ -102,11 +102,13 @@ __global__ void __launch_bounds__(256) k_softcomb(SoftArgs A) {
           x = __fsub_rn(x, cff);
           x = __fsub_rn(x, rintf(x));                                 // [-0.5, 0.5] cycles
           float sn, cs;
-          sincospif(2.f * x, &sn, &cs);
+          sincospi_reduced(2.f * x, sn, cs);
           float zr = sg * cs, zi = -sg * sn;
           const float tt = __fmul_rn((float)((int64_t)(2 * tau) - A.tc2), 0.5e-6f);  // s
           float ss, sc;
-          sincospif(2.f * __fmul_rn(A.delta_hz, tt), &ss, &sc);
+          float xs = __fmul_rn(A.delta_hz, tt);  // cycles, folded to [-1/2, 1/2]
+          xs = __fsub_rn(xs, rintf(xs));
+          sincospi_reduced(2.f * xs, ss, sc);
           const float ur = sc, ui = -ss;
           const float wtt = kTwoPi * tt;
 #pragma unroll
