@@ -46,6 +46,11 @@ METRIC = "NDFT event-bin terms/s (1280x720, 8 windows x 4 streams per CUDA-graph
 UNIT = "terms/s"
 SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 OPS_PER_TERM = 3  # FP32 FMA-pipe lane-ops per term of the blocked three-multiplication form
+# DRAM bytes (read + write) per active pixel of one launch, from one ncu capture
+# of each kernel on a 640x360 window of the same recipe (profiles/
+# blocked_ndft_c3_640x360.md, profiles/comb_c3_640x360.md); scaled to a launch
+# by its active pixels, since both kernels' traffic is per-pixel rows
+TRAFFIC_PER_PIXEL = {"k_blocked<6,1,0>": 2867.0, "k_comb<0>": 3043.0}
 
 
 def _gen_window(args):
@@ -480,8 +485,14 @@ def main():
     else:
         ndft_ms, kern = statistics.mean(spec_ms), "blocked NDFT spectrum kernel (k_blocked<TB,1,0>)"
     achieved = OPS_PER_TERM * terms_step / (ndft_ms * 1e-3) / 1e12
+    n_act = sum(active_of(w, W, H) for w in wins)
+    tb = 6 if nb <= 768 and nb > 512 else None  # rows per lane the launcher picks for 750 bins
+    tr_ndft = (TRAFFIC_PER_PIXEL["k_blocked<6,1,0>"] * n_act / nwin
+               if (not fused_mode and tb == 6 and int(tuning.get("rows_per_lane", 0)) in (0, 6))
+               else None)
     roof_ndft = dict(bound="alu", achieved=achieved, peak=peak, unit="Tops/s",
-                     frac=achieved / peak, traffic=None, kernel=kern,
+                     frac=achieved / peak, traffic=tr_ndft, traffic_unit="B per launch (window)",
+                     kernel=kern, launches_per_step=nwin, launch_ms=ndft_ms / nwin,
                      kernel_ms_per_step=ndft_ms, share_of_step=ndft_ms / ms_step,
                      peak_source="derived: 152 SMs x 128 FP32 lanes x 2070 MHz",
                      ops="3 FP32 FMA-pipe lane-ops per term (three-multiplication complex "
@@ -489,15 +500,19 @@ def main():
     roof_comb = None
     if not fused_mode:
         pk = measured_peaks()
-        n_act = sum(active_of(w, W, H) for w in wins)
         # algorithmic bytes: read every active pixel's spectrum row, write its
         # four results (4 + 4 + 4 + 1 B), clear the window's mask
         comb_bytes = n_act * (nb * 4 + 13) + nwin * W * H
         comb_t = statistics.mean(comb_ms)
         ach = comb_bytes / (comb_t * 1e-3) / 1e9
         roof_comb = dict(bound="hbm", achieved=ach, peak=pk["hbm_gbs"], unit="GB/s",
-                         frac=ach / pk["hbm_gbs"], traffic=None,
-                         kernel="SF + comb kernel (k_comb<0>)", kernel_ms_per_step=comb_t,
+                         frac=ach / pk["hbm_gbs"],
+                         traffic=TRAFFIC_PER_PIXEL["k_comb<0>"] * n_act / nwin
+                         if nb <= 1024 else None,
+                         traffic_unit="B per launch (window)",
+                         kernel="SF + comb kernel (k_comb<0>)", launches_per_step=nwin,
+                         launch_ms=comb_t / nwin, bytes_per_launch=comb_bytes / nwin,
+                         kernel_ms_per_step=comb_t,
                          share_of_step=comb_t / ms_step, peak_source=pk["source"],
                          bytes_per_step=comb_bytes,
                          note="far below the HBM bound: instruction-issue and latency bound "
