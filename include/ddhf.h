@@ -281,6 +281,23 @@ ddhf_status ddhf_export_scores(ddhf_ctx *ctx, int32_t slot, uint32_t *active, fl
 ddhf_status ddhf_enable_stage_timing(ddhf_ctx *ctx, int32_t enable);
 ddhf_status ddhf_stage_times(ddhf_ctx *ctx, float *out_ms);
 
+/* ddhf_detect over n_windows windows whose event arrays are in HOST memory
+ * (windows[w].x/y/t_us/p host pointers; page-locked memory lets the copies
+ * overlap the kernels): window w + 1's events are copied into one of two
+ * context-owned device staging buffers on an internal copy stream while
+ * window w is processed on `stream` (the same kernels as ddhf_detect, one
+ * window at a time in the context's first slot). Results go to host memory:
+ * boxes_host[n_windows * cap] (window w at boxes_host + w * cap),
+ * n_boxes_host[n_windows], masks_host[n_windows * W * H] (nullable). The call
+ * returns once the work is enqueued; host inputs must stay valid and outputs
+ * are complete when `stream` has finished. The copies are ordered after the
+ * work already queued on `stream`. Any n_windows >= 1 (max_windows does not
+ * apply); the first call allocates the staging buffers (2 x max_events
+ * events). */
+ddhf_status ddhf_detect_batch_host(ddhf_ctx *ctx, const ddhf_window *windows, int32_t n_windows,
+                                   ddhf_box *boxes_host, int32_t cap, int32_t *n_boxes_host,
+                                   uint8_t *masks_host, ddhf_stream stream);
+
 /* Soft comb score and its gradients for the differentiation pattern (not in
  * the paper; built on Eq. 6 and the comb of Eq. 8-10). For each listed pixel
  * a (pixels[n_px]: pixel keys y*W+x of the last binned window) with

@@ -78,6 +78,18 @@ void free_all(Ctx *c) {
   F(c->flags);
   F(c->soft_part);
   F(c->pbuf);
+  F(c->hstage[0]);
+  F(c->hstage[1]);
+  F(c->hbox);
+  F(c->hnbox);
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+  c->copy_stream = nullptr;
+  for (cudaEvent_t *e : {&c->h_ready[0], &c->h_ready[1], &c->h_free[0], &c->h_free[1],
+                         &c->h_start})
+    if (*e) {
+      cudaEventDestroy(*e);
+      *e = nullptr;
+    }
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   c->graph_exec = nullptr;
   for (auto &e : c->stage_ev)
@@ -650,6 +662,91 @@ ddhf_status ddhf_detect_batch(ddhf_ctx *h, const ddhf_window *wins, int32_t n_wi
     c->graph_key = key;
   }
   DDHF_CUDA_TRY(c, cudaGraphLaunch(c->graph_exec, s));
+  c->binned = true;
+  return DDHF_OK;
+}
+
+// Stage sizes of one window's raw events: x, y int16, t int64, p int8.
+static int64_t host_stage_bytes(int64_t n) {
+  const int64_t a = (2 * n + 255) & ~(int64_t)255;
+  return 2 * a + ((8 * n + 255) & ~(int64_t)255) + ((n + 255) & ~(int64_t)255);
+}
+
+ddhf_status ddhf_detect_batch_host(ddhf_ctx *h, const ddhf_window *wins, int32_t n_windows,
+                                   ddhf_box *boxes_host, int32_t cap, int32_t *n_boxes_host,
+                                   uint8_t *masks_host, ddhf_stream stream) {
+  if (!h) return DDHF_ERR_INVALID_ARG;
+  Ctx *c = &h->c;
+  if (!wins || n_windows < 1) return fail(c, DDHF_ERR_INVALID_ARG, "need at least one window");
+  if (!n_boxes_host || cap < 0 || (cap > 0 && !boxes_host))
+    return fail(c, DDHF_ERR_INVALID_ARG, "bad box arguments");
+  for (int w = 0; w < n_windows; ++w)
+    DDHF_TRY(check_window(c, wins[w].x, wins[w].y, wins[w].t_us, wins[w].p, wins[w].n,
+                          wins[w].window_us));
+  // workspace: staging for max_events, a box buffer for cap (grown on demand)
+  if (c->hstage_cap < c->max_events) {
+    for (auto &p : c->hstage) {
+      if (p) cudaFree(p);
+      p = nullptr;
+      DDHF_CUDA_TRY(c, cudaMalloc(&p, host_stage_bytes(std::max<int64_t>(c->max_events, 1))));
+    }
+    c->hstage_cap = c->max_events;
+  }
+  if (c->hbox_cap < std::max(cap, 1)) {
+    if (c->hbox) cudaFree(c->hbox);
+    c->hbox = nullptr;
+    DDHF_CUDA_TRY(c, cudaMalloc(&c->hbox, sizeof(ddhf_box) * std::max(cap, 1)));
+    c->hbox_cap = std::max(cap, 1);
+  }
+  if (!c->hnbox) DDHF_CUDA_TRY(c, cudaMalloc(&c->hnbox, sizeof(int32_t)));
+  if (!c->copy_stream)
+    DDHF_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+  for (cudaEvent_t *e : {&c->h_ready[0], &c->h_ready[1], &c->h_free[0], &c->h_free[1],
+                         &c->h_start})
+    if (!*e) DDHF_CUDA_TRY(c, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaStream_t cs = c->copy_stream;
+  c->last_stream = s;
+  // the copies are ordered after the caller's earlier work on `stream`
+  DDHF_CUDA_TRY(c, cudaEventRecord(c->h_start, s));
+  DDHF_CUDA_TRY(c, cudaStreamWaitEvent(cs, c->h_start, 0));
+  for (int w = 0; w < n_windows; ++w) {
+    const int b = w & 1;
+    const ddhf_window &W = wins[w];
+    const int64_t n = W.n;
+    const int64_t ab2 = (2 * c->hstage_cap + 255) & ~(int64_t)255;
+    const int64_t ab8 = (8 * c->hstage_cap + 255) & ~(int64_t)255;
+    char *base = static_cast<char *>(c->hstage[b]);
+    int16_t *dx = reinterpret_cast<int16_t *>(base);
+    int16_t *dy = reinterpret_cast<int16_t *>(base + ab2);
+    int64_t *dt = reinterpret_cast<int64_t *>(base + 2 * ab2);
+    int8_t *dp = reinterpret_cast<int8_t *>(base + 2 * ab2 + ab8);
+    // window w's events into staging set b once window w - 2 has finished with it
+    if (w >= 2) DDHF_CUDA_TRY(c, cudaStreamWaitEvent(cs, c->h_free[b], 0));
+    if (n > 0) {
+      DDHF_CUDA_TRY(c, cudaMemcpyAsync(dx, W.x, 2 * n, cudaMemcpyHostToDevice, cs));
+      DDHF_CUDA_TRY(c, cudaMemcpyAsync(dy, W.y, 2 * n, cudaMemcpyHostToDevice, cs));
+      DDHF_CUDA_TRY(c, cudaMemcpyAsync(dt, W.t_us, 8 * n, cudaMemcpyHostToDevice, cs));
+      DDHF_CUDA_TRY(c, cudaMemcpyAsync(dp, W.p, n, cudaMemcpyHostToDevice, cs));
+    }
+    DDHF_CUDA_TRY(c, cudaEventRecord(c->h_ready[b], cs));
+    DDHF_CUDA_TRY(c, cudaStreamWaitEvent(s, c->h_ready[b], 0));
+    ddhf_window dw = W;
+    dw.x = dx;
+    dw.y = dy;
+    dw.t_us = dt;
+    dw.p = dp;
+    DDHF_TRY(run_detect(c, &dw, 1, c->hbox, cap, c->hnbox, nullptr, s));
+    DDHF_CUDA_TRY(c, cudaEventRecord(c->h_free[b], s));
+    if (cap > 0)
+      DDHF_CUDA_TRY(c, cudaMemcpyAsync(boxes_host + (int64_t)w * cap, c->hbox,
+                                       sizeof(ddhf_box) * cap, cudaMemcpyDeviceToHost, s));
+    DDHF_CUDA_TRY(c, cudaMemcpyAsync(n_boxes_host + w, c->hnbox, sizeof(int32_t),
+                                     cudaMemcpyDeviceToHost, s));
+    if (masks_host)
+      DDHF_CUDA_TRY(c, cudaMemcpyAsync(masks_host + (int64_t)w * c->npx, c->slots[0].mask,
+                                       c->npx, cudaMemcpyDeviceToHost, s));
+  }
   c->binned = true;
   return DDHF_OK;
 }

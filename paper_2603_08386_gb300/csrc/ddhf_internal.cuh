@@ -116,6 +116,16 @@ struct Ctx {
   bool timing_recorded = false;
   bool timing_fused = true;
   int timing_windows = 0;
+  // host-input detection (ddhf_detect_batch_host): two device staging sets
+  // for one window's raw events, a copy stream and its events, and the
+  // device box buffer of one window
+  void *hstage[2] = {nullptr, nullptr};  // x int16, y int16, t int64, p int8 each
+  int64_t hstage_cap = 0;                // events per staging set
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t h_ready[2] = {nullptr, nullptr}, h_free[2] = {nullptr, nullptr}, h_start = nullptr;
+  ddhf_box *hbox = nullptr;
+  int32_t *hnbox = nullptr;
+  int32_t hbox_cap = 0;
   cudaEvent_t stage_ev[4] = {nullptr, nullptr, nullptr, nullptr};
   std::vector<cudaEvent_t> win_ev;  // 4 per window (unfused path)
   // graph cache of ddhf_detect_batch

@@ -104,6 +104,8 @@ SIGNATURES = {
     "ddhf_spectrum_median": (_I32, [_VP, _VP, _I64, _VP, _VP]),
     "ddhf_power_spectrum_noalloc": (_I32, [ctypes.POINTER(ddhf_grid), _VP, _VP, _I64, _VP, _I64,
                                            _VP, _I64, _VP]),
+    "ddhf_detect_batch_host": (_I32, [_VP, ctypes.POINTER(ddhf_window), _I32, _VP, _I32, _VP,
+                                      _VP, _VP]),
     "ddhf_set_row_offset": (_I32, [_VP, _I32]),
     "ddhf_components": (_I32, [_VP, _VP, _I32, _VP, _I32, _VP, _VP]),
     "ddhf_merge_bands": (_I32, [_I32, _I32, _I32, _VP, _VP, _VP, _VP, ctypes.POINTER(ddhf_params),
@@ -223,6 +225,29 @@ def ddhf_label(ctx, mask, labels, stream=None):
 def ddhf_boxes(ctx, labels, boxes, cap, n_boxes, stream=None):
     _check(load().ddhf_boxes(ctx, _ptr(labels), _ptr(boxes), int(cap), _ptr(n_boxes),
                              _stream(stream)), ctx)
+
+
+def _hptr(t):
+    if t is None:
+        return None
+    if t.is_cuda:
+        raise ValueError("expected a host tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def ddhf_detect_batch_host(ctx, windows, boxes_host, cap, n_boxes_host, masks_host=None,
+                           stream=None):
+    """windows: list of (x, y, t, p, n, t0, window_us) with HOST tensors
+    (pin_memory() for overlap); outputs are host tensors, complete after the
+    stream finishes."""
+    arr = (ddhf_window * len(windows))()
+    for i, (x, y, t, p, n, t0, win) in enumerate(windows):
+        arr[i] = ddhf_window(_hptr(x), _hptr(y), _hptr(t), _hptr(p), int(n), int(t0), int(win))
+    _check(load().ddhf_detect_batch_host(ctx, arr, len(windows), _hptr(boxes_host), int(cap),
+                                         _hptr(n_boxes_host), _hptr(masks_host),
+                                         _stream(stream)), ctx)
 
 
 def ddhf_set_row_offset(ctx, row0):
