@@ -283,7 +283,7 @@ def main():
     ddhf.ddhf_enable_stage_timing(ctx.h, True)
     tuning, tune_note = ddhf.ddhf_get_tuning(ctx.h), "default"
     if not args.no_tune:
-        # the autotuner times the fused kernel on the first 4 windows of this batch
+        # the autotuner times the whole batched call on the first 4 windows of this batch
         from paper_2603_08386_gb300 import tune
         k = min(4, nwin)
         tctx = ddhf.Context(W, H, grid, max_events=max_ev, max_windows=k)

@@ -155,9 +155,13 @@ typedef struct {
  *                   per window, a spectrum kernel writes a context-owned
  *                   buffer that a separate comb kernel reads (more warps per
  *                   SM for the latency-bound comb). Same results either way.
+ *  overlap          with fuse 0 and several windows: 1 runs the comb kernel of
+ *                   window w on a second stream while the spectra of window
+ *                   w + 1 are computed (a second spectrum buffer is allocated
+ *                   when this is first set); 0 runs them one after the other.
  * Defaults: heavy_min 1024, 4 warps per block, blocks_per_sm 0, rows_per_lane
  * 0, fuse 0 (the unfused path needs the context's spectrum buffer, present
- * when n_bins <= 4096; larger grids always run fused).
+ * when n_bins <= 4096; larger grids always run fused), overlap 0.
  * Different tunings give spectra that agree within the FP32 rounding of the
  * summation order; each tuning is deterministic. */
 typedef struct {
@@ -166,7 +170,7 @@ typedef struct {
   int32_t blocks_per_sm;
   int32_t rows_per_lane;
   int32_t fuse;
-  int32_t reserved;
+  int32_t overlap;
 } ddhf_tuning;
 
 const char *ddhf_status_string(ddhf_status s);

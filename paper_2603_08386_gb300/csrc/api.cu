@@ -78,6 +78,15 @@ void free_all(Ctx *c) {
   F(c->flags);
   F(c->soft_part);
   F(c->pbuf);
+  F(c->pbuf2);
+  if (c->aux_stream) cudaStreamDestroy(c->aux_stream);
+  c->aux_stream = nullptr;
+  for (cudaEvent_t *e : {&c->ov_spec[0], &c->ov_spec[1], &c->ov_comb[0], &c->ov_comb[1],
+                         &c->ov_fork, &c->ov_join})
+    if (*e) {
+      cudaEventDestroy(*e);
+      *e = nullptr;
+    }
   F(c->hstage[0]);
   F(c->hstage[1]);
   F(c->hbox);
@@ -217,11 +226,40 @@ ddhf_status run_detect(Ctx *c, const ddhf_window *wins, int nw, ddhf_box *boxes,
     }
     if (c->timing) DDHF_CUDA_TRY(c, record_stage(c, 1, s));
     DDHF_TRY(launch_fused(c, nw, true, nullptr, 0, s));
+  } else if (c->tuning.overlap && c->pbuf2 && nw > 1) {
+    // per window as below, but the comb kernel of window w runs on the aux
+    // stream while the main stream bins window w + 1 and computes its spectra
+    // into the other buffer; a buffer is reused once the comb two windows
+    // back has read it
+    cudaStream_t b = c->aux_stream;
+    DDHF_CUDA_TRY(c, cudaEventRecord(c->ov_fork, s));
+    DDHF_CUDA_TRY(c, cudaStreamWaitEvent(b, c->ov_fork, 0));
+    for (int w = 0; w < nw; ++w) {
+      const ddhf_window &W = wins[w];
+      float *buf = (w & 1) ? c->pbuf2 : c->pbuf;
+      cudaEvent_t *we = c->timing ? &c->win_ev[5 * w] : nullptr;
+      if (we) DDHF_CUDA_TRY(c, record_event(we[0], s));
+      DDHF_CUDA_TRY(c, cudaMemsetAsync(c->qctl, 0, sizeof(uint32_t), s));
+      DDHF_TRY(bin_into(c, w, W.x, W.y, W.t_us, W.p, W.n, W.t0_us, W.window_us, s));
+      if (we) DDHF_CUDA_TRY(c, record_event(we[1], s));
+      if (w >= 2) DDHF_CUDA_TRY(c, cudaStreamWaitEvent(s, c->ov_comb[w & 1], 0));
+      DDHF_TRY(launch_spectrum_slot(c, w, buf, c->npx, s, c->pbuf_ld));
+      if (we) DDHF_CUDA_TRY(c, record_event(we[2], s));
+      DDHF_CUDA_TRY(c, cudaEventRecord(c->ov_spec[w & 1], s));
+      DDHF_CUDA_TRY(c, cudaStreamWaitEvent(b, c->ov_spec[w & 1], 0));
+      Slot &sl = c->slots[w];
+      if (we) DDHF_CUDA_TRY(c, record_event(we[3], b));
+      DDHF_TRY(launch_comb(c, buf, c->npx, sl.log_sf, sl.snr, sl.f0, sl.mask, b, w, c->pbuf_ld));
+      if (we) DDHF_CUDA_TRY(c, record_event(we[4], b));
+      DDHF_CUDA_TRY(c, cudaEventRecord(c->ov_comb[w & 1], b));
+    }
+    DDHF_CUDA_TRY(c, cudaEventRecord(c->ov_join, b));
+    DDHF_CUDA_TRY(c, cudaStreamWaitEvent(s, c->ov_join, 0));
   } else {
     // per window: binning (own heavy list), spectra into the context buffer, comb
     for (int w = 0; w < nw; ++w) {
       const ddhf_window &W = wins[w];
-      cudaEvent_t *we = c->timing ? &c->win_ev[4 * w] : nullptr;
+      cudaEvent_t *we = c->timing ? &c->win_ev[5 * w] : nullptr;
       if (we) DDHF_CUDA_TRY(c, record_event(we[0], s));
       DDHF_CUDA_TRY(c, cudaMemsetAsync(c->qctl, 0, sizeof(uint32_t), s));
       DDHF_TRY(bin_into(c, w, W.x, W.y, W.t_us, W.p, W.n, W.t0_us, W.window_us, s));
@@ -229,9 +267,10 @@ ddhf_status run_detect(Ctx *c, const ddhf_window *wins, int nw, ddhf_box *boxes,
       Slot &sl = c->slots[w];
       DDHF_TRY(launch_spectrum_slot(c, w, c->pbuf, c->npx, s, c->pbuf_ld));
       if (we) DDHF_CUDA_TRY(c, record_event(we[2], s));
+      if (we) DDHF_CUDA_TRY(c, record_event(we[3], s));
       DDHF_TRY(launch_comb(c, c->pbuf, c->npx, sl.log_sf, sl.snr, sl.f0, sl.mask, s, w,
                            c->pbuf_ld));
-      if (we) DDHF_CUDA_TRY(c, record_event(we[3], s));
+      if (we) DDHF_CUDA_TRY(c, record_event(we[4], s));
     }
   }
   c->timing_fused = fused;
@@ -410,10 +449,23 @@ ddhf_status ddhf_set_tuning(ddhf_ctx *h, const ddhf_tuning *t) {
                             t->warps_per_block != 8) ||
       t->blocks_per_sm < 0 || t->blocks_per_sm > 32 ||
       !(r == 0 || r == 1 || r == 2 || r == 4 || r == 6 || r == 8) ||
-      (t->fuse != 0 && t->fuse != 1))
+      (t->fuse != 0 && t->fuse != 1) || (t->overlap != 0 && t->overlap != 1))
     return fail(&h->c, DDHF_ERR_INVALID_ARG, "tuning out of range");
-  h->c.tuning = *t;
-  drop_graph(&h->c);
+  Ctx *c = &h->c;
+  if (t->overlap && c->pbuf && !c->pbuf2) {
+    // second spectrum buffer, a stream and events for overlapped windows
+    if (cudaMalloc(&c->pbuf2, (size_t)c->npx * c->pbuf_ld * sizeof(float)) != cudaSuccess) {
+      c->pbuf2 = nullptr;
+      cudaGetLastError();
+      return fail(c, DDHF_ERR_CUDA, "no memory for a second spectrum buffer");
+    }
+    DDHF_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking));
+    for (cudaEvent_t *e : {&c->ov_spec[0], &c->ov_spec[1], &c->ov_comb[0], &c->ov_comb[1],
+                           &c->ov_fork, &c->ov_join})
+      DDHF_CUDA_TRY(c, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  }
+  c->tuning = *t;
+  drop_graph(c);
   return DDHF_OK;
 }
 
@@ -422,7 +474,7 @@ ddhf_status ddhf_enable_stage_timing(ddhf_ctx *h, int32_t enable) {
   Ctx *c = &h->c;
   if (enable && !c->stage_ev[0]) {
     for (auto &e : c->stage_ev) DDHF_CUDA_TRY(c, cudaEventCreate(&e));
-    c->win_ev.assign(4 * (size_t)c->max_windows, nullptr);
+    c->win_ev.assign(5 * (size_t)c->max_windows, nullptr);
     for (auto &e : c->win_ev) DDHF_CUDA_TRY(c, cudaEventCreate(&e));
   }
   if ((bool)enable != c->timing) drop_graph(c);
@@ -443,10 +495,10 @@ ddhf_status ddhf_stage_times(ddhf_ctx *h, float *out_ms) {
   } else {
     for (int w = 0; w < c->timing_windows; ++w) {
       float b, sp, cb;
-      const cudaEvent_t *we = &c->win_ev[4 * w];
+      const cudaEvent_t *we = &c->win_ev[5 * w];
       DDHF_CUDA_TRY(c, cudaEventElapsedTime(&b, we[0], we[1]));
       DDHF_CUDA_TRY(c, cudaEventElapsedTime(&sp, we[1], we[2]));
-      DDHF_CUDA_TRY(c, cudaEventElapsedTime(&cb, we[2], we[3]));
+      DDHF_CUDA_TRY(c, cudaEventElapsedTime(&cb, we[3], we[4]));
       out_ms[0] += b;
       out_ms[3] += sp;
       out_ms[4] += cb;

@@ -105,6 +105,10 @@ struct Ctx {
   uint32_t *flags = nullptr;     // [1] DDHF_FLAG_* bits
   float *soft_part = nullptr;    // [16 * npx + 16] soft-comb gradient partials
   float *pbuf = nullptr;         // [npx * pbuf_ld] spectra of one window (unfused detection)
+  float *pbuf2 = nullptr;        // a second one for overlapped windows (tuning.overlap)
+  cudaStream_t aux_stream = nullptr;  // comb kernels of overlapped windows
+  cudaEvent_t ov_spec[2] = {nullptr, nullptr}, ov_comb[2] = {nullptr, nullptr};
+  cudaEvent_t ov_fork = nullptr, ov_join = nullptr;
   int64_t pbuf_ld = 0;           // row stride of pbuf: n_bins rounded up to 4 floats
   CombConst comb{};
   GridConst gconst{};
@@ -127,7 +131,7 @@ struct Ctx {
   int32_t *hnbox = nullptr;
   int32_t hbox_cap = 0;
   cudaEvent_t stage_ev[4] = {nullptr, nullptr, nullptr, nullptr};
-  std::vector<cudaEvent_t> win_ev;  // 4 per window (unfused path)
+  std::vector<cudaEvent_t> win_ev;  // 5 per window (unfused path)
   // graph cache of ddhf_detect_batch
   int64_t graph_kernels = 0;
   cudaGraphExec_t graph_exec = nullptr;

@@ -64,7 +64,7 @@ class ddhf_stats(ctypes.Structure):
 class ddhf_tuning(ctypes.Structure):
     _fields_ = [("heavy_min", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("rows_per_lane", ctypes.c_int32),
-                ("fuse", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("fuse", ctypes.c_int32), ("overlap", ctypes.c_int32)]
 
 
 class ddhf_component(ctypes.Structure):
@@ -186,9 +186,9 @@ def ddhf_destroy(ctx):
 
 
 def ddhf_set_tuning(ctx, heavy_min=1024, warps_per_block=4, blocks_per_sm=0, rows_per_lane=0,
-                    fuse=1):
+                    fuse=0, overlap=0):
     t = ddhf_tuning(int(heavy_min), int(warps_per_block), int(blocks_per_sm), int(rows_per_lane),
-                    int(fuse), 0)
+                    int(fuse), int(overlap))
     _check(load().ddhf_set_tuning(ctx, ctypes.byref(t)), ctx)
 
 
@@ -196,7 +196,8 @@ def ddhf_get_tuning(ctx):
     t = ddhf_tuning()
     _check(load().ddhf_get_tuning(ctx, ctypes.byref(t)), ctx)
     return dict(heavy_min=t.heavy_min, warps_per_block=t.warps_per_block,
-                blocks_per_sm=t.blocks_per_sm, rows_per_lane=t.rows_per_lane, fuse=t.fuse)
+                blocks_per_sm=t.blocks_per_sm, rows_per_lane=t.rows_per_lane, fuse=t.fuse,
+                overlap=t.overlap)
 
 
 def ddhf_bin_events(ctx, x, y, t, p, n, t0, window_us, stream=None):

@@ -1,11 +1,11 @@
-"""Autotuner of the persistent blocked kernel (batched detection).
+"""Autotuner of the batched detection call.
 
 Times ``ddhf_detect_batch`` on the caller's own windows for each candidate
-``ddhf_tuning`` (heavy-pixel threshold, warps per block, resident blocks per
-SM, rows per lane), using the library's stage timer around the fused kernel,
-keeps the fastest, sets it on the context, and caches the choice in a JSON
-file keyed by device, sensor, grid, parameters and workload shape, so later
-runs reuse it without timing. Only the launch configuration changes; every
+``ddhf_tuning`` (heavy-pixel threshold, warps per block, rows per lane, fused
+or separate spectrum and comb kernels, overlapped windows) by the wall time
+of the whole call (CUDA events on its stream), keeps the fastest, sets it on
+the context, and caches the choice in a JSON file keyed by device, sensor,
+grid, parameters and workload shape, so later runs reuse it without timing. Only the launch configuration changes; every
 candidate computes the same per-pixel results up to FP32 summation order.
 """
 from __future__ import annotations
@@ -20,11 +20,16 @@ import torch
 from . import ddhf
 
 DEFAULT_CANDIDATES = [
-    dict(heavy_min=hm, warps_per_block=wpb, blocks_per_sm=0, rows_per_lane=r, fuse=f)
-    for f in (1, 0)
+    dict(heavy_min=hm, warps_per_block=wpb, blocks_per_sm=0, rows_per_lane=r, fuse=1, overlap=0)
     for hm in (512, 1024, 4096)
     for wpb in (4, 8)
     for r in (0, 4)
+] + [
+    dict(heavy_min=hm, warps_per_block=wpb, blocks_per_sm=0, rows_per_lane=r, fuse=0, overlap=ov)
+    for hm in (512, 1024, 4096)
+    for wpb in (4, 8)
+    for r in (0, 4)
+    for ov in (0, 1)
 ]
 
 
@@ -39,11 +44,18 @@ def workload_key(ctx: "ddhf.Context", windows) -> str:
     return hashlib.sha1(json.dumps(sig, sort_keys=True).encode()).hexdigest()[:16]
 
 
-def _time_fused(ctx, windows, boxes, cap, nbox, reps):
+def _time_call(ctx, windows, boxes, cap, nbox, reps):
+    """Median wall time (CUDA events on the stream) of the whole batched call;
+    the first, capturing call is not counted."""
     ms = []
     for _ in range(reps + 1):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
         ddhf.ddhf_detect_batch(ctx.h, windows, boxes, cap, nbox, None, use_graph=True)
-        ms.append(ddhf.ddhf_stage_times(ctx.h)[1])
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
     return statistics.median(ms[1:])
 
 
@@ -62,13 +74,12 @@ def autotune(ctx: "ddhf.Context", windows, boxes, cap, nbox, candidates=None, re
         best = cache[key]["tuning"]
         ctx.set_tuning(**best)
         return best, cache[key].get("timings", {})
-    ddhf.ddhf_enable_stage_timing(ctx.h, True)
     timings = {}
     best, best_ms = None, None
     for cand in cands:
         try:
             ctx.set_tuning(**cand)
-            ms = _time_fused(ctx, windows, boxes, cap, nbox, reps)
+            ms = _time_call(ctx, windows, boxes, cap, nbox, reps)
         except ddhf.DDHFError:
             continue  # a candidate that does not fit (shared memory) is skipped
         timings[json.dumps(cand, sort_keys=True)] = ms
@@ -78,7 +89,7 @@ def autotune(ctx: "ddhf.Context", windows, boxes, cap, nbox, candidates=None, re
         raise RuntimeError("no tuning candidate could be launched")
     ctx.set_tuning(**best)
     if cache_path:
-        cache[key] = dict(tuning=best, fused_ms=best_ms, timings=timings)
+        cache[key] = dict(tuning=best, call_ms=best_ms, timings=timings)
         tmp = cache_path + f".tmp{os.getpid()}"
         with open(tmp, "w") as f:
             json.dump(cache, f, indent=1, sort_keys=True)

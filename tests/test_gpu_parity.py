@@ -357,8 +357,10 @@ def test_batch_graph_equals_single_windows():
     nbx = torch.zeros(len(scenes), dtype=torch.int32, device="cuda")
     masks = torch.empty((len(scenes), W * H), dtype=torch.uint8, device="cuda")
     ddhf.ddhf_enable_stage_timing(cb.h, True)
-    for fuse, use_graph in ((1, False), (1, True), (1, True), (0, False), (0, True), (0, True)):
-        cb.set_tuning(fuse=fuse)
+    for fuse, overlap, use_graph in ((1, 0, False), (1, 0, True), (1, 0, True), (0, 0, False),
+                                     (0, 0, True), (0, 0, True), (0, 1, False), (0, 1, True),
+                                     (0, 1, True)):
+        cb.set_tuning(fuse=fuse, overlap=overlap)
         boxes.fill_(-7)
         masks.fill_(3)
         ddhf.ddhf_detect_batch(cb.h, wins, boxes, cap, nbx, masks, use_graph=use_graph)
