@@ -532,6 +532,11 @@ def main():
                                            spectra=statistics.mean(spec_ms),
                                            comb=statistics.mean(comb_ms),
                                            labels_boxes=statistics.mean(box_ms)),
+                    stage_note=("per-stage CUDA-event durations; with the overlap tuning the "
+                                "comb of one window runs beside the binning and spectra of the "
+                                "next, so stages overlap in time and their sum exceeds the step"
+                                if int(tuning.get("overlap", 0)) else
+                                "per-stage CUDA-event durations, stages in sequence"),
                     l2="inputs 8.3 GB per step, larger than L2; no flush",
                     tuning=dict(tuning, how=tune_note),
                     parallelism=f"replicas x{world}"),
