@@ -308,9 +308,12 @@ def test_detect_c1_matches_oracle():
     assert gm[dk].mean() > 0.5
 
 
-def test_fused_equals_unfused_bitwise():
+@pytest.mark.parametrize("nb,step", [(750, 2), (2000, 1)])
+def test_fused_equals_unfused_bitwise(nb, step):
+    # 750 bins: the fast comb; 2000 bins: the generic comb (fused kernel and
+    # separate comb kernel alike)
     s = synth.small_scene(41, W=64, H=48, n_noise=60_000, drone_px=150,
-                          grid=synth.hz_grid(0, 2, 750))
+                          grid=synth.hz_grid(0, step, nb))
     for heavy_min in (32, 1024):
         c = ctx_for(s, heavy_min=heavy_min, fuse=1)
         x, y, t, p = ddhf.events_to_device(s)
