@@ -984,34 +984,48 @@ __device__ __forceinline__ CombOut comb_warp_fast(const float *Pw, const CombCon
     __syncwarp();
   }
 
-  // ---- phase 2: exact SNR of the surviving candidates, one per lane: the
-  // band mask of H(w) and its bins below the band from the bin codes
+  // ---- phase 2: exact SNR of the surviving candidates, 32 at a time, one
+  // per lane. The band mask of H(w) and its bins below the band are gathered
+  // from the bin codes by a group of g lanes per candidate (g the largest
+  // power of two with nk g <= 32; each lane takes every g-th bin of H(w)) and
+  // combined within the group, then handed to the candidate's lane.
   const uint32_t outside = bw >= 32 ? 0u : (0xFFFFFFFFu << bw);
   float best = 0.f;
   int bestw = -1;
   for (int i0 = 0; i0 < n_items; i0 += 32) {
     const int nk = min(32, n_items - i0);
     const int wl = lane < nk ? (use_list ? (int)list[i0 + lane] : cc.w_lo + i0 + lane) : 1;
-    int my_below = 0;
-    uint32_t my_mask = 0u;
-    if (lane < nk) {
+    const int g = nk > 16 ? 1 : nk > 8 ? 2 : nk > 4 ? 4 : nk > 2 ? 8 : nk > 1 ? 16 : 32;
+    const int gk = lane / g, gs = lane - gk * g;
+    const int wk = __shfl_sync(0xffffffffu, wl, gk < nk ? gk : 0);
+    uint32_t gmask = 0u;
+    int gbelow = 0;
+    if (gk < nk) {
       int mvk = M;
-      while (mvk * wl > L) --mvk;
-      int j_lo = wl - d, j_hi = mvk * wl + d;  // overlapping windows: one range
-      const int nwin = wl >= 2 * d + 1 ? mvk : 1;
-      for (int m = 1; m <= nwin; ++m) {
-        if (wl >= 2 * d + 1) {
-          j_lo = m * wl - d;
-          j_hi = m * wl + d;
+      while (mvk * wk > L) --mvk;
+      if (wk >= 2 * d + 1) {
+        for (int m = 1; m <= mvk; ++m) {
+          for (int i = gs - d; i <= d; i += g) {
+            const uint32_t k = code[m * wk + i];
+            gmask |= __funnelshift_lc(0u, 1u, k);  // 1 << k, 0 for k >= 32
+            gbelow += (int)((k >> 5) & 1u);
+          }
         }
-#pragma unroll 7
-        for (int j = j_lo; j <= j_hi; ++j) {
+      } else {  // overlapping windows: one range
+        for (int j = wk - d + gs; j <= mvk * wk + d; j += g) {
           const uint32_t k = code[j];
-          my_mask |= __funnelshift_lc(0u, 1u, k);  // 1 << k, 0 for k >= 32
-          my_below += (int)((k >> 5) & 1u);
+          gmask |= __funnelshift_lc(0u, 1u, k);
+          gbelow += (int)((k >> 5) & 1u);
         }
       }
     }
+    for (int o = g >> 1; o > 0; o >>= 1) {
+      gmask |= __shfl_xor_sync(0xffffffffu, gmask, o);
+      gbelow += __shfl_xor_sync(0xffffffffu, gbelow, o);
+    }
+    const int lead = lane * g < 32 ? lane * g : 0;
+    const uint32_t my_mask = __shfl_sync(0xffffffffu, gmask, lead);
+    const int my_below = __shfl_sync(0xffffffffu, gbelow, lead);
     const bool ok = lane < nk;
     const int w = wl;
     int pos0 = 0, pos1 = 0, c = 0, mv = 1;

@@ -484,35 +484,45 @@ ddhf_status launch_blocked_t(Ctx *c, int n_slots, float *P, int64_t cap_px, cuda
   return DDHF_OK;
 }
 
-template <bool FUSED>
-ddhf_status launch_blocked_any(Ctx *c, int n_slots, float *P, int64_t cap_px, cudaStream_t s,
-                               int slot0 = 0, int64_t ld = 0) {
+// One kernel instantiation per rows-per-lane choice TB, for comb variant NW.
+template <int NW, bool FUSED>
+ddhf_status launch_blocked_tb(Ctx *c, int n_slots, float *P, int64_t cap_px, cudaStream_t s,
+                              int slot0, int64_t ld) {
   const int nbr = c->gconst.nbr;
   int tb = std::min(8, (nbr + 3) / 4);
   tb = tb <= 2 ? tb : tb <= 4 ? 4 : tb <= 6 ? 6 : 8;
   if (c->tuning.rows_per_lane > 0) tb = c->tuning.rows_per_lane;
-  // fused: the fast comb where it applies, else the generic one with 8 mask words
-  const int variant = comb_variant(c->comb);
-#define DDHF_TB_CASE(T)                                                           \
-  case T:                                                                         \
-    if constexpr (!FUSED) {                                                       \
-      return launch_blocked_t<T, 1, false>(c, n_slots, P, cap_px, s, slot0, ld);  \
-    } else {                                                                      \
-      if (variant == 0)                                                           \
-        return launch_blocked_t<T, 0, true>(c, n_slots, P, cap_px, s, slot0, ld); \
-      return launch_blocked_t<T, 8, true>(c, n_slots, P, cap_px, s, slot0, ld);   \
-    }
   switch (tb) {
-    DDHF_TB_CASE(1)
-    DDHF_TB_CASE(2)
-    DDHF_TB_CASE(4)
-    DDHF_TB_CASE(6)
-    DDHF_TB_CASE(8)
+    case 1: return launch_blocked_t<1, NW, FUSED>(c, n_slots, P, cap_px, s, slot0, ld);
+    case 2: return launch_blocked_t<2, NW, FUSED>(c, n_slots, P, cap_px, s, slot0, ld);
+    case 4: return launch_blocked_t<4, NW, FUSED>(c, n_slots, P, cap_px, s, slot0, ld);
+    case 6: return launch_blocked_t<6, NW, FUSED>(c, n_slots, P, cap_px, s, slot0, ld);
+    case 8: return launch_blocked_t<8, NW, FUSED>(c, n_slots, P, cap_px, s, slot0, ld);
   }
-#undef DDHF_TB_CASE
   return DDHF_ERR_UNSUPPORTED;
 }
 
+// The fused kernels with the generic comb (1 or 8 mask words) are
+// instantiated in their own translation unit.
+extern template ddhf_status launch_blocked_tb<1, true>(Ctx *, int, float *, int64_t, cudaStream_t,
+                                                       int, int64_t);
+extern template ddhf_status launch_blocked_tb<8, true>(Ctx *, int, float *, int64_t, cudaStream_t,
+                                                       int, int64_t);
+
+template <bool FUSED>
+ddhf_status launch_blocked_any(Ctx *c, int n_slots, float *P, int64_t cap_px, cudaStream_t s,
+                               int slot0 = 0, int64_t ld = 0) {
+  if constexpr (!FUSED) {
+    return launch_blocked_tb<1, false>(c, n_slots, P, cap_px, s, slot0, ld);
+  } else {
+    // the comb variant of the spectrum size: fast, or generic with 1 or 8 mask words
+    switch (comb_variant(c->comb)) {
+      case 0: return launch_blocked_tb<0, true>(c, n_slots, P, cap_px, s, slot0, ld);
+      case 1: return launch_blocked_tb<1, true>(c, n_slots, P, cap_px, s, slot0, ld);
+      default: return launch_blocked_tb<8, true>(c, n_slots, P, cap_px, s, slot0, ld);
+    }
+  }
+}
 
 }  // namespace blocked
 }  // namespace ddhf
