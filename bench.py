@@ -44,6 +44,9 @@ from paper_2603_08386_gb300 import synth  # noqa: E402
 N_STREAMS, N_WINDOWS = 4, 8
 METRIC = "NDFT event-bin terms/s (1280x720, 8 windows x 4 streams per CUDA-graph launch)"
 UNIT = "terms/s"
+WORKLOAD = ("C3: {W}x{H}, 8 consecutive 30 ms windows x 4 streams per step, Pareto(1.5) "
+            "per-pixel counts capped at 20k, 3 drones; grid 0-1498 Hz step 2 Hz (750 bins); "
+            "Table 2 parameters")
 SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 OPS_PER_TERM = 3  # FP32 FMA-pipe lane-ops per term of the blocked three-multiplication form
 # DRAM bytes (read + write) per active pixel of one launch, from one ncu capture
@@ -218,8 +221,8 @@ def run_reference(args):
                 steps=args.steps, warmup=args.warmup, ms_per_step=1e3 * tot_s / args.steps,
                 higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
                 data="synthetic",
-                config=dict(workload="C3 1280x720 30 ms windows, ~20M events/window, 750 bins; "
-                                     "oracle on pixel samples"),
+                config=dict(workload=WORKLOAD.format(W=1280, H=720),
+                            sample="oracle on seeded pixel samples of window 0 of stream 0"),
                 cpu_baseline=dict(value=v, unit=UNIT, cores=1, kind="oracle", sample=sample),
                 e2e=dict(value=v, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
@@ -523,9 +526,7 @@ def main():
         metric=metric, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
         warmup=args.warmup, ms_per_step=ms_step, higher_is_better=True, scaling="weak",
         vs_baseline=None, dtype="f32", data="synthetic",
-        config=dict(workload=f"C3: {W}x{H}, 8 consecutive 30 ms windows x 4 streams per step, "
-                             "Pareto(1.5) per-pixel counts capped at 20k, 3 drones; "
-                             "grid 0-1498 Hz step 2 Hz (750 bins); Table 2 parameters",
+        config=dict(workload=WORKLOAD.format(W=W, H=H),
                     windows_per_step=nwin, events_per_step=events_step,
                     terms_per_step=terms_step, ms_per_window=ms_step / nwin,
                     stage_ms_per_step=dict(binning=statistics.mean(bin_ms), classify=f_avg,
