@@ -50,9 +50,8 @@ WORKLOAD = ("C3: {W}x{H}, 8 consecutive 30 ms windows x 4 streams per step, Pare
 SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 OPS_PER_TERM = 3  # FP32 FMA-pipe lane-ops per term of the blocked three-multiplication form
 # DRAM bytes (read + write) per active pixel of one launch, from one ncu capture
-# of each kernel on a 640x360 window of the same recipe (profiles/
-# blocked_ndft_c3_640x360.md, profiles/comb_c3_640x360.md); scaled to a launch
-# by its active pixels, since both kernels' traffic is per-pixel rows
+# of each kernel on a 640x360 window of the same recipe; scaled to a launch by
+# its active pixels, since both kernels' traffic is per-pixel rows
 TRAFFIC_PER_PIXEL = {"k_blocked<6,1,0>": 2867.0, "k_comb<0>": 3043.0}
 
 

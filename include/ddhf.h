@@ -45,7 +45,7 @@ typedef enum {
   DDHF_ERR_CUDA = 2,        /* a CUDA runtime call failed (message in last_error) */
   DDHF_ERR_CAPACITY = 3,    /* an output or workspace was too small */
   DDHF_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
-  DDHF_ERR_UNSUPPORTED = 5, /* a configuration this build does not handle */
+  DDHF_ERR_UNSUPPORTED = 5, /* a configuration the library does not handle */
   DDHF_ERR_STATE = 6        /* calls out of order (e.g. spectrum before binning) */
 } ddhf_status;
 
