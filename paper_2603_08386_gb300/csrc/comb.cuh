@@ -589,10 +589,61 @@ __device__ __forceinline__ int nth_set_bit(uint32_t x, int k) {
   return (k == 0 && (x & 1u)) ? pos : -1;
 }
 
+// The band of full ranks [lo_r, hi_r] (bw <= 32 ranks) of Pw[0..N) in the
+// (value, index) order, exactly, by radix selection of its two ends: lane p
+// gets the value bits and bin of rank lo_r + p. Returns true when the count
+// found disagrees with bw (an internal error). Kept out of line: it runs only
+// for spectra whose middle ranks the histogram cannot separate.
+__device__ __noinline__ static bool comb_band_exact(const float *Pw, int N, int lo_r, int hi_r,
+                                                    int bw, uint32_t *hist, uint32_t &bv_bits,
+                                                    int &bj) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = lanemask_lt();
+  const uint64_t klo = select_rank_slow(Pw, N, lo_r, hist);
+  const uint64_t khi = select_rank_slow(Pw, N, hi_r, hist);
+  uint64_t key = ~0ull;
+  uint32_t run = 0;
+  for (int j0 = 0; j0 < N; j0 += 32) {
+    const int j = j0 + lane;
+    const uint64_t k = j < N ? bin_key(Pw, j) : ~0ull;
+    const bool in = j < N && k >= klo && k <= khi;
+    const uint32_t bi = __ballot_sync(0xffffffffu, in);
+    const uint32_t slot = run + __popc(bi & lt);
+#pragma unroll 1
+    for (uint32_t m = bi; m; m &= m - 1) {  // lane `slot` receives the key
+      const int srcl = __ffs(m) - 1;
+      const uint64_t kk = __shfl_sync(0xffffffffu, k, srcl);
+      const uint32_t sl = __shfl_sync(0xffffffffu, slot, srcl);
+      if ((uint32_t)lane == sl) key = kk;
+    }
+    run += __popc(bi);
+  }
+  key = warp_sort32_u64(key);
+  bv_bits = (uint32_t)(key >> 16);
+  bj = (int)(key & 0xFFFFu);
+  return (int)run != bw;
+}
+
 // Bin j (value v) lies below the band that starts at (T, tj) in the
 // (value, index) order.
 __device__ __forceinline__ bool below_band(float v, int j, float T, int tj) {
   return v < T || (v == T && j < tj);
+}
+
+// Window maxima and bin codes for any half-width d (the d = 3 case has an
+// inline quad version); out of line.
+__device__ __noinline__ static void comb_records_any_d(const float *Pw, int N, int d, float T,
+                                                       int tj, float *rec, uint8_t *code) {
+  const int lane = threadIdx.x & 31;
+  for (int c = lane; c < N; c += 32) {
+    float mx = 0.f;
+    if (c >= d && c <= N - 1 - d) {
+      mx = Pw[c - d];
+      for (int i = 1; i <= 2 * d; ++i) mx = fmaxf(mx, Pw[c - d + i]);
+    }
+    rec[c] = mx;
+    code[c] = below_band(Pw[c], c, T, tj) ? 32u : 64u;
+  }
 }
 
 __device__ __forceinline__ CombOut comb_warp_fast(const float *Pw, const CombConst &cc,
@@ -769,30 +820,10 @@ __device__ __forceinline__ CombOut comb_warp_fast(const float *Pw, const CombCon
     __syncwarp();
   }
   if (slow) {
-    // exact band [lo_r, hi_r] by radix selection
-    const uint64_t klo = select_rank_slow(Pw, N, lo_r, hist);
-    const uint64_t khi = select_rank_slow(Pw, N, hi_r, hist);
-    uint64_t key = ~0ull;
-    uint32_t run = 0;
-    for (int j0 = 0; j0 < N; j0 += 32) {
-      const int j = j0 + lane;
-      const uint64_t k = j < N ? bin_key(Pw, j) : ~0ull;
-      const bool in = j < N && k >= klo && k <= khi;
-      const uint32_t bi = __ballot_sync(0xffffffffu, in);
-      const uint32_t slot = run + __popc(bi & lt);
-#pragma unroll 1
-      for (uint32_t m = bi; m; m &= m - 1) {  // lane `slot` receives the key
-        const int srcl = __ffs(m) - 1;
-        const uint64_t kk = __shfl_sync(0xffffffffu, k, srcl);
-        const uint32_t sl = __shfl_sync(0xffffffffu, slot, srcl);
-        if ((uint32_t)lane == sl) key = kk;
-      }
-      run += __popc(bi);
-    }
-    if ((int)run != bw) bad = true;
-    key = warp_sort32_u64(key);
-    bv = __uint_as_float((uint32_t)(key >> 16));
-    bj = (int)(key & 0xFFFFu);
+    // exact band [lo_r, hi_r] by radix selection (a rare, out-of-line path)
+    uint32_t bvu = 0u;
+    bad |= comb_band_exact(Pw, N, lo_r, hi_r, bw, hist, bvu, bj);
+    bv = __uint_as_float(bvu);
     T = __shfl_sync(0xffffffffu, bv, 0);
     tj = __shfl_sync(0xffffffffu, bj, 0);
     __syncwarp();
@@ -845,15 +876,7 @@ __device__ __forceinline__ CombOut comb_warp_fast(const float *Pw, const CombCon
       }
     }
   } else {
-    for (int c = lane; c < N; c += 32) {
-      float mx = 0.f;
-      if (c >= d && c <= N - 1 - d) {
-        mx = Pw[c - d];
-        for (int i = 1; i <= 2 * d; ++i) mx = fmaxf(mx, Pw[c - d + i]);
-      }
-      rec[c] = mx;
-      code[c] = below_band(Pw[c], c, T, tj) ? 32u : 64u;
-    }
+    comb_records_any_d(Pw, N, d, T, tj, rec, code);
   }
   __syncwarp();
   if (lane < bw) code[bj] = (uint8_t)lane;
