@@ -459,7 +459,9 @@ ddhf_status ddhf_set_tuning(ddhf_ctx *h, const ddhf_tuning *t) {
       cudaGetLastError();
       return fail(c, DDHF_ERR_CUDA, "no memory for a second spectrum buffer");
     }
-    DDHF_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking));
+    int lo_prio = 0, hi_prio = 0;
+    DDHF_CUDA_TRY(c, cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio));
+    DDHF_CUDA_TRY(c, cudaStreamCreateWithPriority(&c->aux_stream, cudaStreamNonBlocking, hi_prio));
     for (cudaEvent_t *e : {&c->ov_spec[0], &c->ov_spec[1], &c->ov_comb[0], &c->ov_comb[1],
                            &c->ov_fork, &c->ov_join})
       DDHF_CUDA_TRY(c, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
