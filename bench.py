@@ -239,6 +239,8 @@ def main():
     ap.add_argument("--windows", type=int, default=N_STREAMS * N_WINDOWS,
                     help="windows per step (default 32; fewer only for profiling cases)")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default tuning)")
+    ap.add_argument("--tuning", default=None,
+                    help="JSON dict of ddhf_tuning fields to use instead of the autotuner")
     ap.add_argument("--procs", type=int, default=int(os.environ.get("DDHF_GEN_PROCS", "16")))
     ap.add_argument("--no-latency", action="store_true", help="skip the one-window latency")
     ap.add_argument("--no-softcomb", action="store_true", help="skip the soft-comb timing")
@@ -284,7 +286,10 @@ def main():
     nbox = torch.zeros(nwin, dtype=torch.int32, device="cuda")
     ddhf.ddhf_enable_stage_timing(ctx.h, True)
     tuning, tune_note = ddhf.ddhf_get_tuning(ctx.h), "default"
-    if not args.no_tune:
+    if args.tuning:
+        ctx.set_tuning(**json.loads(args.tuning))
+        tuning, tune_note = ddhf.ddhf_get_tuning(ctx.h), "given on the command line"
+    elif not args.no_tune:
         # the autotuner times the whole batched call on the first 4 windows of this batch
         from paper_2603_08386_gb300 import tune
         k = min(4, nwin)
