@@ -26,7 +26,7 @@ DEFAULT_CANDIDATES = [
     for r in (0, 4)
 ] + [
     dict(heavy_min=hm, warps_per_block=wpb, blocks_per_sm=0, rows_per_lane=r, fuse=0, overlap=ov)
-    for hm in (512, 1024, 4096)
+    for hm in (128, 256, 512, 1024, 4096)
     for wpb in (4, 8)
     for r in (0, 4)
     for ov in (0, 1)
