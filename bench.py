@@ -68,6 +68,82 @@ def _gen_c4(b):
     return sc.x, sc.y, sc.t, sc.p, sc.t0, sc.window_us, sc.n
 
 
+def slide_leg(wins, W, H, grid, torch, ddhf, hop_us=3750, rebuild_every=64, cap_box=256,
+              warm_passes=2):
+    """The sliding window on one C3 stream (consecutive windows of stream 0):
+    a 30 ms window advanced by hop_us per push. The pushes that fill the first
+    window are untimed; every later push (event delta of hop_us in and out)
+    and the detection that follows it are timed one by one with CUDA events.
+    A second pass with rebuild_every = 1 times pushes that recompute the whole
+    window's state instead."""
+    T, t0 = int(wins[0][5]), int(wins[0][4])
+    x = np.concatenate([w[0] for w in wins])
+    y = np.concatenate([w[1] for w in wins])
+    t = np.concatenate([w[2] for w in wins])
+    p = np.concatenate([w[3] for w in wins])
+    order = np.argsort(t, kind="stable")
+    x, y, t, p = x[order], y[order], t[order], p[order]
+    n_hops = (len(wins) * T) // hop_us
+    fill = T // hop_us
+    bounds = np.searchsorted(t, t0 + hop_us * np.arange(n_hops + 1))
+    per = np.diff(bounds)
+    cap = int(max(per[i:i + fill + 1].sum() for i in range(n_hops)) * 1.05) + 1
+    d = [torch.from_numpy(a).cuda() for a in (x, y, t, p)]
+    sc = ddhf.Context(W, H, grid, max_events=cap)
+    bx = torch.empty((cap_box, 5), dtype=torch.int32, device="cuda")
+    nb = torch.zeros(1, dtype=torch.int32, device="cuda")
+
+    def run(every):
+        sc.slide_begin(T, t0, cap, every)
+        ev, st0 = [], None
+        for i in range(n_hops):
+            lo, hi = int(bounds[i]), int(bounds[i + 1])
+            if i == fill:
+                st0 = sc.slide_stats()
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record()
+            ddhf.ddhf_slide_push(sc.h, d[0][lo:hi], d[1][lo:hi], d[2][lo:hi], d[3][lo:hi],
+                                 hi - lo, t0 + hop_us * (i + 1))
+            e[1].record()
+            ddhf.ddhf_slide_detect(sc.h, bx, cap_box, nb)
+            e[2].record()
+            if i >= fill:
+                ev.append(e)
+        st1 = sc.slide_stats()
+        torch.cuda.synchronize()
+        push = np.array([a.elapsed_time(b) for a, b, _ in ev])
+        det = np.array([b.elapsed_time(c) for _, b, c in ev])
+        delta = (st1["n_added"] - st0["n_added"]) + (st1["n_expired"] - st0["n_expired"])
+        return push, det, delta, st1
+
+    for _ in range(warm_passes):
+        run(rebuild_every)
+    push, det, delta, st = run(rebuild_every)
+    rpush, rdet, _, _ = run(1)
+    sc.stats()
+    sc.close()
+    nbins = grid[3]
+    n = len(push)
+    return dict(
+        workload=f"C3 stream 0 ({W}x{H}), consecutive 30 ms windows; the window advances "
+                 f"{hop_us} us per push; {n} timed pushes after the {fill} that fill it",
+        window_us=T, hop_us=hop_us, rebuild_every=rebuild_every, timed_pushes=n,
+        events_per_hop=float(np.mean(per[fill:])), delta_events_per_hop=delta / n,
+        push_ms_median=float(np.median(push)), detect_ms_median=float(np.median(det)),
+        hop_ms_median=float(np.median(push + det)),
+        delta_terms_per_s=delta * nbins / (push.sum() * 1e-3),
+        rebuild_push_ms_median=float(np.median(rpush)),
+        amortised_hop_ms=float(np.median(push + det)
+                               + (np.median(rpush) - np.median(push)) / rebuild_every),
+        state_bytes=W * H * ((nbins + 31) // 32 * 32) * 8, window_events_last=st["n_window"],
+        pixels_last_push=st["last_pixels"],
+        # algorithmic bytes of a push: each touched pixel's state row read and
+        # written (n_bins complex FP32), the delta's packed words read
+        push_state_gbs=(st["last_pixels"] * nbins * 16 + delta / n * 8) / (np.median(push) * 1e-3)
+        / 1e9,
+        unit="ms per hop (CUDA events); delta terms = (events in + events out) x bins")
+
+
 def rank_seed(rank: int) -> int:
     """Seed of a rank's batch: ranks are independent replicas (weak scaling)."""
     return 1003 + 1000 * rank
@@ -244,6 +320,7 @@ def main():
     ap.add_argument("--procs", type=int, default=int(os.environ.get("DDHF_GEN_PROCS", "16")))
     ap.add_argument("--no-latency", action="store_true", help="skip the one-window latency")
     ap.add_argument("--no-softcomb", action="store_true", help="skip the soft-comb timing")
+    ap.add_argument("--no-slide", action="store_true", help="skip the sliding-window timing")
     ap.add_argument("--softcomb-windows", type=int, default=2)
     ap.add_argument("--latency-replays", type=int, default=100)
     ap.add_argument("--sensor", default="1280x720",
@@ -391,6 +468,12 @@ def main():
                    events=int(wins[0][6]), replays=len(lt), median_ms=float(q50),
                    iqr_ms=float(q75 - q25), p95_ms=float(q95), min_ms=float(lt.min()))
         lc.close()
+    # ------------------------------------------------------------ sliding window
+    slide = None
+    if not args.no_slide and nwin >= 2:
+        slide = slide_leg(wins[:2], W, H, grid, torch, ddhf)
+        if lat:
+            slide["full_window_ms_median"] = lat["median_ms"]
     # ------------------------------------------------------------ soft comb and its adjoint
     # every active pixel of each 640x480 window: S and dS/d(f0, w, sigma) for
     # 6 harmonics x (2Q+1) = 42 evaluation frequencies per pixel
@@ -551,6 +634,7 @@ def main():
         e2e=e2e,
         window_latency=lat,
         softcomb=softc,
+        slide=slide,
         gpu_launches=int(graph_kernels) * args.steps,
         clocks=clk,
         plain=plain,

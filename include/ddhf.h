@@ -401,6 +401,78 @@ ddhf_status ddhf_merge_bands(int32_t W, int32_t H, int32_t n_bands, const int32_
                              const int64_t *comp_off, const ddhf_params *params,
                              ddhf_box *boxes, int32_t cap, int32_t *n_boxes);
 
+/* ------------------------------------------------------ sliding window
+ * Sec. 3.3 notes that the direct NDFT can add the contribution of each event
+ * on its own as it arrives. These calls keep Eq. 6 current while a window of
+ * window_us slides over one event stream: the context holds, per pixel, the
+ * complex sum F_j = sum_k p_k e^{-2 pi i a_j (t_k - t_begin) / denom} over
+ * the events in the window (phases from exact integer residues, as in
+ * ddhf_power_spectrum) and the window's event count, and each push adds the
+ * terms of the events that enter and subtracts those of the events that
+ * leave. |F_j|^2 equals Eq. 6's P_j over the window [t_end - window_us,
+ * t_end) (the time origin only multiplies F_j by a unit phase factor).
+ * Memory: W*H*ceil32(n_bins)*8 bytes of state plus 12 bytes per ring entry.
+ * A context has at most one sliding window. It shares the context's
+ * workspace and slot 0 with ddhf_detect and friends, so calls on one context
+ * must be ordered (one stream, or events between streams). Pushes depend on
+ * host-side ring bookkeeping, so they are not for stream capture. */
+
+/* Counters of the sliding window (ddhf_slide_get_stats). */
+typedef struct {
+  int64_t t_end_us;    /* end of the window after the last push */
+  int64_t pushes;      /* pushes since ddhf_slide_begin */
+  int64_t rebuilds;    /* pushes that recomputed the state from the window's events */
+  int64_t n_added;     /* events added, all pushes */
+  int64_t n_dropped;   /* pushed events not added (time, sensor or polarity) */
+  int64_t n_expired;   /* events that have left the window */
+  int64_t n_window;    /* events in the window now */
+  int64_t last_delta;  /* events whose terms the last push evaluated */
+  int64_t last_pixels; /* pixels whose state the last push changed */
+  int64_t ring_used;   /* ring entries held */
+} ddhf_slide_stats;
+
+/* Start (or restart) a sliding window of window_us microseconds over a stream
+ * that begins at t_begin_us: the state is zero and t_end = t_begin_us.
+ * capacity: ring entries (events) held, at least the events of one window
+ * plus those of one push; requires capacity <= max_events and < 2^31.
+ * rebuild_every = R > 0: every R-th push recomputes the state from the events
+ * still in the window instead of updating it, so the FP32 rounding of at most
+ * R - 1 updates accumulates in F (R = 1: every push recomputes); R = 0: never.
+ * Allocates the state (synchronises the device). */
+ddhf_status ddhf_slide_begin(ddhf_ctx *ctx, int64_t window_us, int64_t t_begin_us,
+                             int64_t capacity, int32_t rebuild_every);
+
+/* Release the sliding window's state (synchronises the device). */
+ddhf_status ddhf_slide_end(ddhf_ctx *ctx);
+
+/* Advance the window to end at t_end_us (>= the previous end). Events x, y, t_us,
+ * p (device arrays of n, n may be 0; any order) are added when
+ * max(t_prev, t_end_us - window_us) <= t < t_end_us (t_prev = the previous end),
+ * the pixel is on the sensor (row offset applied) and the polarity is valid;
+ * the others are dropped and counted. Events with t < t_end_us - window_us
+ * leave the window. Returns DDHF_ERR_CAPACITY, with nothing done, when the
+ * ring cannot hold the push. */
+ddhf_status ddhf_slide_push(ddhf_ctx *ctx, const int16_t *x, const int16_t *y,
+                            const int64_t *t_us, const int8_t *p, int64_t n, int64_t t_end_us,
+                            ddhf_stream stream);
+
+/* Spectra of the window: the pixels with at least n_min events in the window
+ * become slot 0's active list (ascending keys; ddhf_export_scores(ctx, 0, ...)
+ * reads it and the counts) and P[a*n_bins + j] = |F_j|^2 of the a-th of them
+ * (FP32; rows beyond cap_px are not written and raise DDHF_FLAG_CAPACITY;
+ * cap_px = 0 lists the pixels only). */
+ddhf_status ddhf_slide_spectra(ddhf_ctx *ctx, float *P, int64_t cap_px, ddhf_stream stream);
+
+/* Detection on the current window: the active list as in ddhf_slide_spectra,
+ * then the SF + comb scoring, labelling and boxes of ddhf_detect on |F|^2
+ * (outputs and their layout as in ddhf_detect; slot 0's scores). The comb
+ * kernel squares the state as it reads it: no spectrum buffer is written. */
+ddhf_status ddhf_slide_detect(ddhf_ctx *ctx, ddhf_box *boxes, int32_t cap, int32_t *n_boxes_dev,
+                              uint8_t *mask_out, ddhf_stream stream);
+
+/* Synchronise and read the sliding window's counters (host struct). */
+ddhf_status ddhf_slide_get_stats(ddhf_ctx *ctx, ddhf_slide_stats *out);
+
 /* Synchronise the context's last stream and read its counters and device
  * flags. Returns DDHF_ERR_CAPACITY / DDHF_ERR_TIMEOUT when the matching
  * flag is set (the stats are filled either way); the flags are then cleared. */

@@ -45,6 +45,7 @@ ddhf_status dev_alloc(Ctx *c, T **p, size_t count) {
   } while (0)
 
 void free_all(Ctx *c) {
+  slide_free(c);
   auto F = [](void *p) {
     if (p) cudaFree(p);
   };

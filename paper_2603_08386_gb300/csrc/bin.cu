@@ -32,10 +32,18 @@ struct RawIn {
   uint64_t win;
   int W, H, pol01;
   int row0;  // sensor row of the context's row 0 (row bands)
+  // pre-packed input instead of (x, y, t, p): key pk[e] (kDropKey = not kept)
+  // and value pv[e] as the sort carries them
+  const uint32_t *pk = nullptr, *pv = nullptr;
 };
 
 __device__ __forceinline__ bool load_raw(const RawIn &in, int64_t e, uint32_t &key,
                                          uint32_t &val) {
+  if (in.pk) {
+    key = in.pk[e];
+    val = in.pv[e];
+    return key != kDropKey;
+  }
   int xx = in.x[e], yy = in.y[e] - in.row0;
   int64_t tt = in.t[e];
   int pp = in.p[e];
@@ -370,16 +378,21 @@ ddhf_status launch_scan_u32(Ctx *c, const uint32_t *in, uint32_t *out, int64_t n
   return DDHF_OK;
 }
 
-ddhf_status bin_window(Ctx *c, int slot_i, const int16_t *x, const int16_t *y, const int64_t *t,
-                       const int8_t *p, int64_t n, int64_t t0, int64_t win, cudaStream_t s) {
-  Slot &sl = c->slots[slot_i];
-  sl.t0 = t0;
-  sl.window_us = win;
+// The same for uint64 (the scratch holds n / 2048 + 64 words of 64 bits).
+ddhf_status launch_scan_u64(Ctx *c, const uint64_t *in, uint64_t *out, int64_t n, cudaStream_t s) {
+  DDHF_CUDA_TRY(c, scan_rec<uint64_t>(in, out, n, reinterpret_cast<uint64_t *>(c->scan_part),
+                                      nullptr, s));
+  return DDHF_OK;
+}
+
+ddhf_status bin_core(Ctx *c, Slot &sl, const RawIn &raw, int n_min, int heavy_min,
+                     uint64_t *heavy_list, uint32_t *heavy_count, uint32_t slot_tag,
+                     int64_t heavy_cap, cudaStream_t s) {
+  const int64_t n = raw.n;
   const int64_t npx = c->npx;
   uint32_t *ntot = reinterpret_cast<uint32_t *>(c->qctl + 8);  // n_valid of this binning
   DDHF_CUDA_TRY(c, cudaMemsetAsync(ntot, 0, sizeof(uint32_t), s));
   DDHF_CUDA_TRY(c, cudaMemsetAsync(sl.counters, 0, 7 * sizeof(uint64_t), s));
-  RawIn raw{x, y, t, p, n, t0, (uint64_t)win, c->W, c->H, c->params.polarity_01, c->row0};
   const int64_t nch = ceil_div(n, kBinChunk);
   uint32_t *kbuf[2] = {c->keysA, c->keysB};
   uint32_t *vbuf[2] = {c->valsA, c->valsB};
@@ -425,16 +438,34 @@ ddhf_status bin_window(Ctx *c, int slot_i, const int16_t *x, const int16_t *y, c
     DDHF_CUDA_TRY(c, cudaGetLastError());
   }
   unsigned pb = (unsigned)std::min<int64_t>(ceil_div(npx + 1, 256), sm_blocks);
-  k_pack<<<pb, 256, 0, s>>>(c->seg_lo, c->seg_hi, c->packed, npx, c->params.n_min);
+  k_pack<<<pb, 256, 0, s>>>(c->seg_lo, c->seg_hi, c->packed, npx, n_min);
   DDHF_CUDA_TRY(c, cudaGetLastError());
   DDHF_CUDA_TRY(c, scan_rec<uint64_t>(c->packed, c->packed, npx + 1,
                                       reinterpret_cast<uint64_t *>(c->scan_part), nullptr, s));
   k_finish<<<pb, 256, 0, s>>>(c->packed, c->seg_lo, c->seg_hi, sl.offsets, sl.active,
-                              sl.counters, npx, c->params.n_min, c->tuning.heavy_min, n,
-                              c->grid.n_bins, c->work, c->qctl, (uint32_t)slot_i, c->heavy_cap,
-                              c->flags);
+                              sl.counters, npx, n_min, heavy_min, n, c->grid.n_bins, heavy_list,
+                              heavy_count, slot_tag, heavy_cap, c->flags);
   DDHF_CUDA_TRY(c, cudaGetLastError());
   return DDHF_OK;
+}
+
+ddhf_status bin_window(Ctx *c, int slot_i, const int16_t *x, const int16_t *y, const int64_t *t,
+                       const int8_t *p, int64_t n, int64_t t0, int64_t win, cudaStream_t s) {
+  Slot &sl = c->slots[slot_i];
+  sl.t0 = t0;
+  sl.window_us = win;
+  RawIn raw{x, y, t, p, n, t0, (uint64_t)win, c->W, c->H, c->params.polarity_01, c->row0};
+  return bin_core(c, sl, raw, c->params.n_min, c->tuning.heavy_min, c->work, c->qctl,
+                  (uint32_t)slot_i, c->heavy_cap, s);
+}
+
+// Stable sort of pre-packed (key, value) pairs into a slot's per-pixel list;
+// key kDropKey marks pairs that are not kept.
+ddhf_status bin_packed(Ctx *c, Slot &sl, const uint32_t *keys, const uint32_t *vals, int64_t n,
+                       int n_min, int heavy_min, uint64_t *heavy_list, uint32_t *heavy_count,
+                       int64_t heavy_cap, cudaStream_t s) {
+  RawIn raw{nullptr, nullptr, nullptr, nullptr, n, 0, 0, c->W, c->H, 0, 0, keys, vals};
+  return bin_core(c, sl, raw, n_min, heavy_min, heavy_list, heavy_count, 0u, heavy_cap, s);
 }
 
 void set_bin_attributes() {

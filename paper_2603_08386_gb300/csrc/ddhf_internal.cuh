@@ -20,6 +20,7 @@ constexpr int kBinRounds = 4;      // rounds per chunk
 constexpr int kBinChunk = kBinThreads * kBinItems * kBinRounds;  // 8192 events
 constexpr int kMaxBandWords = 8;   // comb rank band up to 256 positions
 constexpr uint32_t kSignBit = 0x80000000u;
+constexpr uint32_t kDropKey = 0xffffffffu;  // pre-packed sort input: pair not kept
 
 // Per-window binning output and per-pixel results (one "slot" per window).
 struct Slot {
@@ -72,6 +73,8 @@ struct GridConst {
   int32_t nbr;        // b-rows of the blocked form: ceil(N / 32)
   float two_over_denom;
 };
+
+struct SlideState;  // sliding-window spectra (slide.cu)
 
 struct Ctx {
   int W = 0, H = 0;
@@ -136,6 +139,7 @@ struct Ctx {
   int64_t graph_kernels = 0;
   cudaGraphExec_t graph_exec = nullptr;
   std::vector<uint8_t> graph_key;
+  SlideState *slide = nullptr;  // ddhf_slide_begin .. ddhf_slide_end
 };
 
 // ---------------------------------------------------------------- helpers
@@ -207,8 +211,15 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 // bin.cu
 ddhf_status bin_window(Ctx *c, int slot, const int16_t *x, const int16_t *y, const int64_t *t,
                        const int8_t *p, int64_t n, int64_t t0, int64_t win, cudaStream_t s);
+ddhf_status bin_packed(Ctx *c, Slot &sl, const uint32_t *keys, const uint32_t *vals, int64_t n,
+                       int n_min, int heavy_min, uint64_t *heavy_list, uint32_t *heavy_count,
+                       int64_t heavy_cap, cudaStream_t s);
 ddhf_status launch_scan_u32(Ctx *c, const uint32_t *in, uint32_t *out, int64_t n,
                             cudaStream_t s);
+ddhf_status launch_scan_u64(Ctx *c, const uint64_t *in, uint64_t *out, int64_t n,
+                            cudaStream_t s);
+// slide.cu
+void slide_free(Ctx *c);
 // ndft.cu
 ddhf_status launch_spectrum(Ctx *c, int form, float *P, int64_t cap_px, cudaStream_t s);
 ddhf_status launch_spectrum_slot(Ctx *c, int slot, float *P, int64_t cap_px, cudaStream_t s,
@@ -216,6 +227,10 @@ ddhf_status launch_spectrum_slot(Ctx *c, int slot, float *P, int64_t cap_px, cud
 ddhf_status launch_comb(Ctx *c, const float *P, int64_t cap_px, float *log_sf, float *snr,
                         int32_t *f0, uint8_t *mask, cudaStream_t s, int slot = 0,
                         int64_t ld = 0);
+// comb_cplx.cu: the comb on complex rows F (row of active pixel a at
+// F + active[a] * ldF) of slot 0's active list
+ddhf_status launch_comb_cplx(Ctx *c, const float2 *F, int64_t ldF, float *log_sf, float *snr,
+                             int32_t *f0, uint8_t *mask, cudaStream_t s);
 ddhf_status launch_fused(Ctx *c, int n_slots, bool write_p, float *P, int64_t cap_px,
                          cudaStream_t s);
 void set_bin_attributes();

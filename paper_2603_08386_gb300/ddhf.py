@@ -75,6 +75,12 @@ class ddhf_box(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in ("x0", "y0", "x1", "y1", "n_px")]
 
 
+class ddhf_slide_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in (
+        "t_end_us", "pushes", "rebuilds", "n_added", "n_dropped", "n_expired", "n_window",
+        "last_delta", "last_pixels", "ring_used")]
+
+
 # exported symbol -> (restype, argtypes)
 _VP, _I32, _I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
 SIGNATURES = {
@@ -110,6 +116,12 @@ SIGNATURES = {
     "ddhf_components": (_I32, [_VP, _VP, _I32, _VP, _I32, _VP, _VP]),
     "ddhf_merge_bands": (_I32, [_I32, _I32, _I32, _VP, _VP, _VP, _VP, ctypes.POINTER(ddhf_params),
                                 _VP, _I32, _VP]),
+    "ddhf_slide_begin": (_I32, [_VP, _I64, _I64, _I64, _I32]),
+    "ddhf_slide_end": (_I32, [_VP]),
+    "ddhf_slide_push": (_I32, [_VP, _VP, _VP, _VP, _VP, _I64, _I64, _VP]),
+    "ddhf_slide_spectra": (_I32, [_VP, _VP, _I64, _VP]),
+    "ddhf_slide_detect": (_I32, [_VP, _VP, _I32, _VP, _VP, _VP]),
+    "ddhf_slide_get_stats": (_I32, [_VP, ctypes.POINTER(ddhf_slide_stats)]),
 }
 
 _lib = None
@@ -375,6 +387,35 @@ def ddhf_get_stats(ctx, raise_on_flags=True):
     return out
 
 
+def ddhf_slide_begin(ctx, window_us, t_begin_us, capacity, rebuild_every=64):
+    _check(load().ddhf_slide_begin(ctx, int(window_us), int(t_begin_us), int(capacity),
+                                   int(rebuild_every)), ctx)
+
+
+def ddhf_slide_end(ctx):
+    _check(load().ddhf_slide_end(ctx), ctx)
+
+
+def ddhf_slide_push(ctx, x, y, t, p, n, t_end_us, stream=None):
+    _check(load().ddhf_slide_push(ctx, _ptr(x), _ptr(y), _ptr(t), _ptr(p), int(n),
+                                  int(t_end_us), _stream(stream)), ctx)
+
+
+def ddhf_slide_spectra(ctx, P, cap_px, stream=None):
+    _check(load().ddhf_slide_spectra(ctx, _ptr(P), int(cap_px), _stream(stream)), ctx)
+
+
+def ddhf_slide_detect(ctx, boxes, cap, n_boxes, mask_out=None, stream=None):
+    _check(load().ddhf_slide_detect(ctx, _ptr(boxes), int(cap), _ptr(n_boxes), _ptr(mask_out),
+                                    _stream(stream)), ctx)
+
+
+def ddhf_slide_get_stats(ctx):
+    s = ddhf_slide_stats()
+    _check(load().ddhf_slide_get_stats(ctx, ctypes.byref(s)), ctx)
+    return {k: getattr(s, k) for k, _ in ddhf_slide_stats._fields_}
+
+
 # ---------------------------------------------------------------- convenience
 
 class Context:
@@ -474,6 +515,36 @@ class Context:
 
     def stats(self, raise_on_flags=True):
         return ddhf_get_stats(self.h, raise_on_flags)
+
+    # sliding window (Sec. 3.3: terms of the events entering and leaving)
+    def slide_begin(self, window_us, t_begin_us, capacity=None, rebuild_every=64):
+        cap = self.max_events if capacity is None else capacity
+        ddhf_slide_begin(self.h, window_us, t_begin_us, cap, rebuild_every)
+
+    def slide_push(self, x, y, t, p, t_end_us):
+        ddhf_slide_push(self.h, x, y, t, p, x.numel(), t_end_us)
+
+    def slide_spectra(self):
+        """(active keys, P [n_active, n_bins]) of the current window."""
+        ddhf_slide_spectra(self.h, None, 0)
+        act = self.scores()["active"]
+        na = act.numel()
+        P = torch.empty((max(na, 1), self.n_bins), dtype=torch.float32, device=self.dev)
+        ddhf_slide_spectra(self.h, P, na)
+        return act, P[:na]
+
+    def slide_detect(self, cap=4096, want_mask=False):
+        bx = torch.empty((max(cap, 1), 5), dtype=torch.int32, device=self.dev)
+        nb = torch.zeros(1, dtype=torch.int32, device=self.dev)
+        mask = torch.empty(self.npx, dtype=torch.uint8, device=self.dev) if want_mask else None
+        ddhf_slide_detect(self.h, bx, cap, nb, mask)
+        return bx, nb, mask
+
+    def slide_stats(self):
+        return ddhf_slide_get_stats(self.h)
+
+    def slide_end(self):
+        ddhf_slide_end(self.h)
 
 
 def events_to_device(scene, device="cuda"):

@@ -345,6 +345,41 @@ def small_scene(seed: int, W: int = 48, H: int = 40, window_us: int = 20_000,
     return s
 
 
+def slide_stream(seed: int, W: int = 48, H: int = 40, duration_us: int = 80_000,
+                 n_noise: int = 60_000, drone_px: int = 150, f0_hz: float = 150.0,
+                 n_hot: int = 3, hot_events: int = 6000, t_base: int = 0, grid=None,
+                 extra_invalid: int = 0) -> Scene:
+    """A seeded event stream over [t_base, t_base + duration_us) for the
+    sliding-window tests: one drone, heavy-tailed bursty noise and n_hot
+    pixels with hot_events uniform events each (many per hop), in time order
+    up to the generator's granularity; optional invalid events (bad x/y/p)."""
+    rng = np.random.default_rng(seed)
+    npx = W * H
+    parts, info, dk = _drones(rng, W, H, [(W // 2, H // 2, drone_px, f0_hz)], 0.0,
+                              duration_us, per_edge=3)
+    x_m = max(n_noise / npx / 3.0, 0.3)
+    counts = _pareto_counts(rng, npx, x_m, cap=max(n_noise // 8, 8))
+    counts[dk] = 0
+    parts.append(_bursty(rng, np.arange(npx), counts, 0.0, duration_us))
+    if n_hot:
+        hot = rng.choice(np.setdiff1d(np.arange(npx), dk), n_hot, replace=False)
+        parts.append(_uniform(rng, hot, np.full(n_hot, hot_events), 0.0, duration_us))
+    g = grid if grid is not None else hz_grid(0, 10, 100)
+    s = _assemble(W, H, t_base, duration_us, parts, g, rng, info, dict(config="stream"))
+    if extra_invalid:
+        m = int(extra_invalid)
+        bx = rng.integers(-3, W + 3, m).astype(np.int16)
+        by = rng.integers(-3, H + 3, m).astype(np.int16)
+        bp = rng.choice(np.array([-1, 1, 0, 2], np.int8), m)
+        bt = rng.integers(0, duration_us, m).astype(np.int64) + t_base
+        at = np.searchsorted(s.t, bt)
+        s.x = np.insert(s.x, at, bx)
+        s.y = np.insert(s.y, at, by)
+        s.t = np.insert(s.t, at, bt)
+        s.p = np.insert(s.p, at, bp)
+    return s
+
+
 def synthetic_spectra(n_px: int, N: int, seed: int) -> np.ndarray:
     """Seeded FP32 power spectra [n_px, N] for scoring tests: exponential noise
     rows, rows with harmonic combs (one or two fundamentals, peaks spread over
