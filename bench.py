@@ -20,6 +20,11 @@ pipeline on the same windows, and the FP64 oracle timed on a sample.
 --sensor WxH runs the same recipe on a smaller sensor (profiling captures
 only; the headline workload is 1280x720).
 
+The `slide` object times the sliding window (Sec. 3.3: the terms of the
+events that enter and leave a window that advances 3.75 ms per push) on the
+first C3 stream; --only-slide runs just that leg (for launch-list captures),
+--slide-warm sets its untimed passes.
+
 Under torchrun every rank runs its own 32 windows (seeded by rank; weak
 scaling, no data-path collective); rank 0 prints one JSON line.
 """
@@ -321,6 +326,9 @@ def main():
     ap.add_argument("--no-latency", action="store_true", help="skip the one-window latency")
     ap.add_argument("--no-softcomb", action="store_true", help="skip the soft-comb timing")
     ap.add_argument("--no-slide", action="store_true", help="skip the sliding-window timing")
+    ap.add_argument("--only-slide", action="store_true",
+                    help="run only the sliding-window leg and print its object (profiling)")
+    ap.add_argument("--slide-warm", type=int, default=2, help="untimed sliding-window passes")
     ap.add_argument("--softcomb-windows", type=int, default=2)
     ap.add_argument("--latency-replays", type=int, default=100)
     ap.add_argument("--sensor", default="1280x720",
@@ -351,6 +359,11 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     grid = synth.hz_grid(0, 2, 750)
     nb = grid[3]
+    if args.only_slide:
+        if rank == 0:
+            print(json.dumps(dict(slide=slide_leg(wins[:2], W, H, grid, torch, ddhf,
+                                                  warm_passes=args.slide_warm))), flush=True)
+        return
     terms_step = sum(terms_of(w, W, H, nb) for w in wins)
     events_step = sum(w[6] for w in wins)
     max_ev = max(w[6] for w in wins)
@@ -471,7 +484,7 @@ def main():
     # ------------------------------------------------------------ sliding window
     slide = None
     if not args.no_slide and nwin >= 2:
-        slide = slide_leg(wins[:2], W, H, grid, torch, ddhf)
+        slide = slide_leg(wins[:2], W, H, grid, torch, ddhf, warm_passes=args.slide_warm)
         if lat:
             slide["full_window_ms_median"] = lat["median_ms"]
     # ------------------------------------------------------------ soft comb and its adjoint
