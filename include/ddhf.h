@@ -191,6 +191,12 @@ ddhf_status ddhf_create(int32_t W, int32_t H, const ddhf_grid *grid,
 ddhf_status ddhf_destroy(ddhf_ctx *ctx);
 
 ddhf_status ddhf_set_tuning(ddhf_ctx *ctx, const ddhf_tuning *tuning);
+
+/* Replace the thresholds of Sec. 3.4-3.5 (same requirements as for
+ * ddhf_create; params is a host pointer). Later binning, scoring and box
+ * calls use them; a cached ddhf_detect_batch graph is dropped. This is what
+ * a hyperparameter search over Table 2's ranges calls between evaluations. */
+ddhf_status ddhf_set_params(ddhf_ctx *ctx, const ddhf_params *params);
 ddhf_status ddhf_get_tuning(const ddhf_ctx *ctx, ddhf_tuning *out);
 
 /* Sec. 3.5 "Event processing": keep events with t0 <= t < t0+window_us,

@@ -512,6 +512,17 @@ ddhf_status ddhf_stage_times(ddhf_ctx *h, float *out_ms) {
   return DDHF_OK;
 }
 
+ddhf_status ddhf_set_params(ddhf_ctx *h, const ddhf_params *params) {
+  if (!h) return DDHF_ERR_INVALID_ARG;
+  Ctx *c = &h->c;
+  const ddhf_status st = check_params(params);
+  if (st != DDHF_OK) return fail(c, st, "parameters out of range");
+  c->params = *params;
+  derive_constants(c);
+  drop_graph(c);
+  return DDHF_OK;
+}
+
 ddhf_status ddhf_get_tuning(const ddhf_ctx *h, ddhf_tuning *out) {
   if (!h || !out) return DDHF_ERR_INVALID_ARG;
   *out = h->c.tuning;

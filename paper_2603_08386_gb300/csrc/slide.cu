@@ -185,31 +185,43 @@ struct UpdArgs {
 };
 
 // Partial sums over the packed events ev[e0, e1) at bins j0 + lane + 32 m,
-// m < TPL: per event, the exact residue of the lane's first bin and of a
-// 32-bin step, their phasors, then TPL - 1 rotations. a_mod = a_{j0+lane} mod denom.
+// m < TPL, as two rotation chains of TPL / 2 bins: chain A starts at bin
+// j0 + lane, chain B at bin j0 + lane + 32 TPL / 2. Per event: the exact
+// residues of both first bins and of a 32-bin step, their phasors, then
+// TPL / 2 - 1 rotations of both chains at once in paired FP32 instructions
+// (real parts of A and B in one float2, imaginary parts in another):
+//   re' = re ur - im ui,  im' = re ui + im ur,  each element rounded on its own.
+// accR[m] = (A_m, B_m) real sums, accI[m] the imaginary ones.
 template <int TPL>
 __device__ __forceinline__ void slide_terms(const uint32_t *__restrict__ ev, int64_t e0,
-                                            int64_t e1, uint64_t a_mod, const GridConst &g,
-                                            float2 (&acc)[TPL], int lane) {
+                                            int64_t e1, uint64_t a_mod_a, uint64_t a_mod_b,
+                                            const GridConst &g, float2 (&accR)[TPL / 2],
+                                            float2 (&accI)[TPL / 2], int lane) {
   for (int64_t c0 = e0; c0 < e1; c0 += 32) {
     const uint32_t mine = (c0 + lane < e1) ? ev[c0 + lane] : 0u;
     const int ne = (int)(e1 - c0 < 32 ? e1 - c0 : 32);
     for (int e = 0; e < ne; ++e) {
       const uint32_t w = __shfl_sync(kFull, mine, e);
       const uint64_t tau = w & 0x7fffffffu;
-      const uint64_t r = mod_barrett(a_mod * tau, g.denom, g.barrett);
-      const uint64_t st = mod_barrett(g.da32_mod * tau, g.denom, g.barrett);
-      float2 z = phasor_of_residue(r, g.two_over_denom);
-      const float2 u = phasor_of_residue(st, g.two_over_denom);
-      if (w & kSignBit) {
-        z.x = -z.x;
-        z.y = -z.y;
-      }
+      const float2 za =
+          phasor_of_residue(mod_barrett(a_mod_a * tau, g.denom, g.barrett), g.two_over_denom);
+      const float2 zb =
+          phasor_of_residue(mod_barrett(a_mod_b * tau, g.denom, g.barrett), g.two_over_denom);
+      const float2 u =
+          phasor_of_residue(mod_barrett(g.da32_mod * tau, g.denom, g.barrett), g.two_over_denom);
+      const float sg = (w & kSignBit) ? -1.f : 1.f;
+      float2 R = make_float2(sg * za.x, sg * zb.x), I = make_float2(sg * za.y, sg * zb.y);
+      const float2 UR = make_float2(u.x, u.x), UI = make_float2(u.y, u.y);
+      const float2 NUI = make_float2(-u.y, -u.y);
 #pragma unroll
-      for (int m = 0; m < TPL; ++m) {
-        acc[m].x = __fadd_rn(acc[m].x, z.x);
-        acc[m].y = __fadd_rn(acc[m].y, z.y);
-        if (m + 1 < TPL) z = cmul(z, u);
+      for (int m = 0; m < TPL / 2; ++m) {
+        accR[m] = __fadd2_rn(accR[m], R);
+        accI[m] = __fadd2_rn(accI[m], I);
+        if (m + 1 < TPL / 2) {
+          const float2 t1 = __fmul2_rn(R, UR), t2 = __fmul2_rn(R, UI);
+          R = __ffma2_rn(I, NUI, t1);
+          I = __ffma2_rn(I, UR, t2);
+        }
       }
     }
   }
@@ -222,67 +234,77 @@ __device__ __forceinline__ uint64_t first_bin_mod(const GridConst &g, int j) {
 template <int TPL>
 __device__ void slide_pixel_warp(const UpdArgs &A, uint32_t k, int64_t e0, int64_t e1,
                                  int lane) {
+  constexpr int HALF = TPL / 2;
   const int N = A.g.N;
   float2 *Fk = A.F + (int64_t)k * A.ldF;
   for (int j0 = 0; j0 < N; j0 += 32 * TPL) {
-    // the state's loads go out first and land while the terms are summed
-    float2 f[TPL], acc[TPL];
+    float2 accR[HALF], accI[HALF];
 #pragma unroll
-    for (int m = 0; m < TPL; ++m) {
-      const int j = j0 + lane + 32 * m;
-      f[m] = j < N ? Fk[j] : make_float2(0.f, 0.f);
-      acc[m] = make_float2(0.f, 0.f);
-    }
-    slide_terms<TPL>(A.ev, e0, e1, first_bin_mod(A.g, j0 + lane), A.g, acc, lane);
+    for (int m = 0; m < HALF; ++m) accR[m] = accI[m] = make_float2(0.f, 0.f);
+    slide_terms<TPL>(A.ev, e0, e1, first_bin_mod(A.g, j0 + lane),
+                     first_bin_mod(A.g, j0 + lane + 32 * HALF), A.g, accR, accI, lane);
 #pragma unroll
-    for (int m = 0; m < TPL; ++m) {
-      const int j = j0 + lane + 32 * m;
-      if (j < N) Fk[j] = make_float2(__fadd_rn(f[m].x, acc[m].x), __fadd_rn(f[m].y, acc[m].y));
+    for (int m = 0; m < HALF; ++m) {
+      const int ja = j0 + lane + 32 * m, jb = ja + 32 * HALF;
+      if (ja < N) {
+        const float2 f = Fk[ja];
+        Fk[ja] = make_float2(__fadd_rn(f.x, accR[m].x), __fadd_rn(f.y, accI[m].x));
+      }
+      if (jb < N) {
+        const float2 f = Fk[jb];
+        Fk[jb] = make_float2(__fadd_rn(f.x, accR[m].y), __fadd_rn(f.y, accI[m].y));
+      }
     }
   }
 }
 
 // A whole block on one pixel: warp w sums the w-th eighth of the events; the
-// eight partials of each bin are added in warp order through shared memory.
+// eight partials of each bin are added in warp order through shared memory,
+// chain A's bins first, then chain B's.
 template <int TPL>
 __device__ void slide_pixel_block(const UpdArgs &A, uint32_t k, int64_t e0, int64_t e1,
                                   float2 *red) {
+  constexpr int HALF = TPL / 2;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int N = A.g.N;
   const int64_t n = e1 - e0;
   const int64_t lo = e0 + n * warp / kSlideWarps, hi = e0 + n * (warp + 1) / kSlideWarps;
   float2 *Fk = A.F + (int64_t)k * A.ldF;
   for (int j0 = 0; j0 < N; j0 += 32 * TPL) {
-    float2 acc[TPL];
+    float2 accR[HALF], accI[HALF];
 #pragma unroll
-    for (int m = 0; m < TPL; ++m) acc[m] = make_float2(0.f, 0.f);
-    slide_terms<TPL>(A.ev, lo, hi, first_bin_mod(A.g, j0 + lane), A.g, acc, lane);
+    for (int m = 0; m < HALF; ++m) accR[m] = accI[m] = make_float2(0.f, 0.f);
+    slide_terms<TPL>(A.ev, lo, hi, first_bin_mod(A.g, j0 + lane),
+                     first_bin_mod(A.g, j0 + lane + 32 * HALF), A.g, accR, accI, lane);
 #pragma unroll
-    for (int m = 0; m < TPL; ++m) red[warp * 32 * TPL + 32 * m + lane] = acc[m];
-    __syncthreads();
-    for (int b = threadIdx.x; b < 32 * TPL; b += kSlideThreads) {
-      const int j = j0 + b;  // slot 32 m + lane holds bin j0 + lane + 32 m
-      if (j < N) {
-        float2 s = red[b];
-        for (int w = 1; w < kSlideWarps; ++w) {
-          s.x = __fadd_rn(s.x, red[w * 32 * TPL + b].x);
-          s.y = __fadd_rn(s.y, red[w * 32 * TPL + b].y);
+    for (int c = 0; c < 2; ++c) {
+#pragma unroll
+      for (int m = 0; m < HALF; ++m)
+        red[warp * 32 * HALF + 32 * m + lane] =
+            c == 0 ? make_float2(accR[m].x, accI[m].x) : make_float2(accR[m].y, accI[m].y);
+      __syncthreads();
+      for (int b = threadIdx.x; b < 32 * HALF; b += kSlideThreads) {
+        const int j = j0 + 32 * HALF * c + b;  // slot 32 m + lane: bin j0 + lane + 32 m (+ chain)
+        if (j < N) {
+          float2 sm = red[b];
+          for (int w = 1; w < kSlideWarps; ++w) {
+            sm.x = __fadd_rn(sm.x, red[w * 32 * HALF + b].x);
+            sm.y = __fadd_rn(sm.y, red[w * 32 * HALF + b].y);
+          }
+          const float2 f = Fk[j];
+          Fk[j] = make_float2(__fadd_rn(f.x, sm.x), __fadd_rn(f.y, sm.y));
         }
-        float2 f = Fk[j];
-        f.x = __fadd_rn(f.x, s.x);
-        f.y = __fadd_rn(f.y, s.y);
-        Fk[j] = f;
       }
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 
 // Persistent: blocks take heavy delta pixels first, then warps take the
 // others in grabs of kSlideGrab.
 template <int TPL>
-__global__ void __launch_bounds__(kSlideThreads) k_slide_update(UpdArgs A) {
-  __shared__ float2 red[kSlideWarps * 32 * TPL];
+__global__ void __launch_bounds__(kSlideThreads, 3) k_slide_update(UpdArgs A) {
+  __shared__ float2 red[kSlideWarps * 32 * (TPL / 2)];
   __shared__ uint32_t item;
   const int lane = threadIdx.x & 31;
   const int64_t nh = (int64_t)A.ctl[0];
@@ -389,11 +411,11 @@ ddhf_status salloc(Ctx *c, T **p, size_t count) {
   return DDHF_OK;
 }
 
-// Bins per lane per pass: the largest of 16, 12, 8 with the fewest padded bins.
+// Bins per lane per pass: the largest of 24, 16, 8 with the fewest padded bins.
 int choose_tpl(int N) {
-  int best = 16;
+  int best = 24;
   int64_t best_pad = -1;
-  for (int t : {16, 12, 8}) {
+  for (int t : {24, 16, 8}) {
     const int64_t span = 32 * t;
     const int64_t pad = ceil_div(N, span) * span;
     if (best_pad < 0 || pad < best_pad) {
@@ -416,8 +438,8 @@ ddhf_status launch_update(Ctx *c, SlideState *S, cudaStream_t s) {
     occ = std::max(occ, 1);                                                                   \
     k_slide_update<TPLV><<<c->num_sms * occ, kSlideThreads, 0, s>>>(A);                       \
   }
-  if (S->tpl == 16) DDHF_SLIDE_CASE(16)
-  else if (S->tpl == 12) DDHF_SLIDE_CASE(12)
+  if (S->tpl == 24) DDHF_SLIDE_CASE(24)
+  else if (S->tpl == 16) DDHF_SLIDE_CASE(16)
   else DDHF_SLIDE_CASE(8)
 #undef DDHF_SLIDE_CASE
   DDHF_CUDA_TRY(c, cudaGetLastError());

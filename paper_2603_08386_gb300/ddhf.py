@@ -90,6 +90,7 @@ SIGNATURES = {
                            _I64, _I32, ctypes.POINTER(_VP)]),
     "ddhf_destroy": (_I32, [_VP]),
     "ddhf_set_tuning": (_I32, [_VP, ctypes.POINTER(ddhf_tuning)]),
+    "ddhf_set_params": (_I32, [_VP, ctypes.POINTER(ddhf_params)]),
     "ddhf_get_tuning": (_I32, [_VP, ctypes.POINTER(ddhf_tuning)]),
     "ddhf_bin_events": (_I32, [_VP, _VP, _VP, _VP, _VP, _I64, _I64, _I64, _VP]),
     "ddhf_export_csr": (_I32, [_VP, _VP, _VP, _I64, _VP, _VP, _VP]),
@@ -202,6 +203,10 @@ def ddhf_set_tuning(ctx, heavy_min=1024, warps_per_block=4, blocks_per_sm=0, row
     t = ddhf_tuning(int(heavy_min), int(warps_per_block), int(blocks_per_sm), int(rows_per_lane),
                     int(fuse), int(overlap))
     _check(load().ddhf_set_tuning(ctx, ctypes.byref(t)), ctx)
+
+
+def ddhf_set_params(ctx, params):
+    _check(load().ddhf_set_params(ctx, ctypes.byref(params)), ctx)
 
 
 def ddhf_get_tuning(ctx):
@@ -443,6 +448,10 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    def set_params(self, params):
+        ddhf_set_params(self.h, params)
+        self.params = params
 
     def set_tuning(self, **kw):
         cur = ddhf_get_tuning(self.h)

@@ -380,6 +380,35 @@ def slide_stream(seed: int, W: int = 48, H: int = 40, duration_us: int = 80_000,
     return s
 
 
+def labelled_scene(seed: int, W: int = 320, H: int = 240, window_us: int = 30_000,
+                   mean_per_px: float = 21.7, grid=None, max_drones: int = 3,
+                   min_sep: int = 140) -> Scene:
+    """A labelled window for detection-quality tests: the C3 noise recipe
+    (bursty, Pareto(1.5) per-pixel counts of mean `mean_per_px`) with 1 to
+    `max_drones` drones of 60-600 rotor pixels at 100-300 Hz blade-pass,
+    centres at least `min_sep` pixels apart. Each drone's ground-truth box
+    (``drones[i]["box"]``) circumscribes its rotor pixels."""
+    rng = np.random.default_rng(seed)
+    npx = W * H
+    n_dr = int(rng.integers(1, max_drones + 1))
+    specs, centres = [], []
+    for _ in range(50 * n_dr):
+        if len(specs) == n_dr:
+            break
+        cx = int(rng.integers(W // 8, W - W // 8))
+        cy = int(rng.integers(H // 8, H - H // 8))
+        if all((cx - a) ** 2 + (cy - b) ** 2 >= min_sep ** 2 for a, b in centres):
+            centres.append((cx, cy))
+            specs.append((cx, cy, int(rng.choice([60, 150, 300, 600])),
+                          float(rng.uniform(100.0, 300.0))))
+    parts, info, dk = _drones(rng, W, H, specs, 0.0, window_us, per_edge=4)
+    counts = _pareto_counts(rng, npx, pareto_x_m(mean_per_px))
+    counts[dk] = rng.poisson(10.0 * window_us * 1e-6, dk.size)
+    parts.append(_bursty(rng, np.arange(npx), counts, 0.0, window_us))
+    g = grid if grid is not None else hz_grid(0, 2, 750)
+    return _assemble(W, H, 0, window_us, parts, g, rng, info, dict(config="labelled"))
+
+
 def synthetic_spectra(n_px: int, N: int, seed: int) -> np.ndarray:
     """Seeded FP32 power spectra [n_px, N] for scoring tests: exponential noise
     rows, rows with harmonic combs (one or two fundamentals, peaks spread over
