@@ -326,6 +326,8 @@ def main():
     ap.add_argument("--no-latency", action="store_true", help="skip the one-window latency")
     ap.add_argument("--no-softcomb", action="store_true", help="skip the soft-comb timing")
     ap.add_argument("--no-slide", action="store_true", help="skip the sliding-window timing")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the one-window blocked / hybrid spectrum timing")
     ap.add_argument("--only-slide", action="store_true",
                     help="run only the sliding-window leg and print its object (profiling)")
     ap.add_argument("--slide-warm", type=int, default=2, help="untimed sliding-window passes")
@@ -481,6 +483,49 @@ def main():
                    events=int(wins[0][6]), replays=len(lt), median_ms=float(q50),
                    iqr_ms=float(q75 - q25), p95_ms=float(q95), min_ms=float(lt.min()))
         lc.close()
+    # ------------------------------------------------------------ spectrum forms, one window
+    # window 0 alone through ddhf_power_spectrum: the blocked kernel on every
+    # active pixel (the FMA-pipe roofline of that kernel, without the hybrid
+    # split) and the hybrid form, whose heavy pixels take the uniform-grid
+    # route (spread + dense product with the shared table)
+    forms = None
+    if not args.no_forms:
+        fc = ddhf.Context(W, H, grid, max_events=max_ev, max_windows=1)
+        d0, w0 = dev[0], wins[0]
+        ddhf.ddhf_bin_events(fc.h, d0[0], d0[1], d0[2], d0[3], w0[6], w0[4], w0[5])
+        na0 = fc.n_active()
+        P0 = torch.empty((max(na0, 1), nb), dtype=torch.float32, device="cuda")
+        hm = int(tuning.get("hybrid_min", 0)) or 64
+        base = {k: v for k, v in tuning.items() if k != "how"}
+        forms = dict(window="stream 0, window 0", active_pixels=na0,
+                     terms=terms_of(w0, W, H, nb))
+        for name, form, tun in (("blocked", ddhf.FORM["blocked"], dict(base, hybrid_min=0)),
+                                ("hybrid", ddhf.FORM["hybrid"], dict(base, hybrid_min=hm))):
+            fc.set_tuning(**tun)
+            for _ in range(3):
+                ddhf.ddhf_power_spectrum(fc.h, form, P0, na0)
+            torch.cuda.synchronize()
+            fe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(10)]
+            for a_, b_ in fe:
+                a_.record()
+                ddhf.ddhf_power_spectrum(fc.h, form, P0, na0)
+                b_.record()
+            torch.cuda.synchronize()
+            forms[name + "_ms"] = float(np.median([a_.elapsed_time(b_) for a_, b_ in fe]))
+        fc.stats()
+        fc.close()
+        cnt0 = _counts(w0, W, H)
+        s_us = grid[2] // (2 * grid[1] * nb)
+        G = (int(w0[5]) - 1) // s_us + 8 if s_us >= 1 else 0
+        thr = max(hm, 16, -(-G // 2))
+        hv = cnt0[cnt0 >= thr] if 16 <= G <= 1024 else cnt0[:0]
+        forms.update(hybrid_min=hm, grid_spacing_us=int(s_us), grid_rows=int(G),
+                     threshold=int(thr), hybrid_pixels=int(hv.size),
+                     hybrid_events=int(hv.sum()),
+                     blocked_tops=OPS_PER_TERM * forms["terms"] / (forms["blocked_ms"] * 1e-3)
+                     / 1e12,
+                     note="hybrid pixels: G grid values each instead of their events")
     # ------------------------------------------------------------ sliding window
     slide = None
     if not args.no_slide and nwin >= 2:
@@ -583,11 +628,22 @@ def main():
     f_avg = statistics.mean(fused_ms)
     fused_mode = statistics.mean(spec_ms) == 0.0
     peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    hybrid_on = not fused_mode and int(tuning.get("hybrid_min", 0)) > 0
     if fused_mode:
         ndft_ms, kern = f_avg, "fused blocked NDFT + SF + comb kernel (k_blocked<TB,NW,1>)"
     else:
         ndft_ms, kern = statistics.mean(spec_ms), "blocked NDFT spectrum kernel (k_blocked<TB,1,0>)"
     achieved = OPS_PER_TERM * terms_step / (ndft_ms * 1e-3) / 1e12
+    ndft_launches, ndft_launch_ms = nwin, ndft_ms / nwin
+    if hybrid_on and forms:
+        # the step's spectrum stage runs the blocked and the hybrid kernels; the
+        # blocked kernel's own rate comes from the one-window FORM_BLOCKED run
+        kern = ("blocked NDFT spectrum kernel (k_blocked<TB,1,0>) on every active pixel of "
+                "one window (ddhf_power_spectrum, FORM_BLOCKED)")
+        achieved = forms["blocked_tops"]
+        ndft_launches, ndft_launch_ms = 1, forms["blocked_ms"]
+    elif hybrid_on:
+        kern += " with the hybrid grid kernels (spectrum stage time)"
     n_act = sum(active_of(w, W, H) for w in wins)
     tb = 6 if nb <= 768 and nb > 512 else None  # rows per lane the launcher picks for 750 bins
     tr_ndft = (TRAFFIC_PER_PIXEL["k_blocked<6,1,0>"] * n_act / nwin
@@ -595,7 +651,7 @@ def main():
                else None)
     roof_ndft = dict(bound="alu", achieved=achieved, peak=peak, unit="Tops/s",
                      frac=achieved / peak, traffic=tr_ndft, traffic_unit="B per launch (window)",
-                     kernel=kern, launches_per_step=nwin, launch_ms=ndft_ms / nwin,
+                     kernel=kern, launches_per_step=ndft_launches, launch_ms=ndft_launch_ms,
                      kernel_ms_per_step=ndft_ms, share_of_step=ndft_ms / ms_step,
                      peak_source="derived: 152 SMs x 128 FP32 lanes x 2070 MHz",
                      ops="3 FP32 FMA-pipe lane-ops per term (three-multiplication complex "
@@ -647,6 +703,7 @@ def main():
         e2e=e2e,
         window_latency=lat,
         softcomb=softc,
+        spectrum_forms=forms,
         slide=slide,
         gpu_launches=int(graph_kernels) * args.steps,
         clocks=clk,

@@ -132,13 +132,27 @@ typedef struct {
  *           split over a thread block. The form used by ddhf_detect.
  *  NAIVE32  precision study only: FP32 phase 2 pi f t from the absolute time.
  *  KAHAN    SINCOS with compensated (Kahan) accumulation.
- *  F64      check path: FP64 phase and accumulation on the GPU. */
+ *  F64      check path: FP64 phase and accumulation on the GPU.
+ *  HYBRID   BLOCKED for most pixels; pixels with at least
+ *           max(hybrid_min, 16, ceil(G/2)) events (hybrid_min from the
+ *           tuning, 64 when it is 0) take the non-uniform FFT route that the
+ *           footnote to Sec. 3.3 mentions: each event, its phase centred on
+ *           the middle bin, is spread onto a uniform time grid of spacing
+ *           s = floor(denom / (2 da n_bins)) us with an "exponential of
+ *           semicircle" kernel of 8 points (Barnett et al. 2019), and the
+ *           grid's G = (window_us - 1) / s + 8 values enter one dense complex
+ *           product with a table shared by all pixels, deconvolved per bin.
+ *           Within about 1e-6 of the exact Eq. 6 power relative to the
+ *           pixel's peak. A window with G < 16 or G > 1024 (or a grid with
+ *           s < 1) runs BLOCKED alone. The first use allocates the path's
+ *           workspace (about 64 bytes per max_events plus 12 KiB per bin). */
 #define DDHF_FORM_SINCOS 0
 #define DDHF_FORM_RECUR 1
 #define DDHF_FORM_BLOCKED 2
 #define DDHF_FORM_NAIVE32 3
 #define DDHF_FORM_KAHAN 4
 #define DDHF_FORM_F64 5
+#define DDHF_FORM_HYBRID 6
 
 /* Launch tuning of the persistent BLOCKED kernel (chosen by the autotuner).
  *  heavy_min   pixels with at least this many events (>= 32) are processed by
@@ -159,9 +173,15 @@ typedef struct {
  *                   window w on a second stream while the spectra of window
  *                   w + 1 are computed (a second spectrum buffer is allocated
  *                   when this is first set); 0 runs them one after the other.
+ *  hybrid_min       with fuse 0: pixels with at least max(hybrid_min, 16,
+ *                   ceil(G/2)) events take the grid route of DDHF_FORM_HYBRID
+ *                   in ddhf_detect / ddhf_detect_batch (its workspace is
+ *                   allocated when this is first set); 0 turns it off. The
+ *                   fused kernel ignores it.
  * Defaults: heavy_min 1024, 4 warps per block, blocks_per_sm 0, rows_per_lane
  * 0, fuse 0 (the unfused path needs the context's spectrum buffer, present
- * when n_bins <= 4096; larger grids always run fused), overlap 0.
+ * when n_bins <= 4096; larger grids always run fused), overlap 0,
+ * hybrid_min 0.
  * Different tunings give spectra that agree within the FP32 rounding of the
  * summation order; each tuning is deterministic. */
 typedef struct {
@@ -171,6 +191,7 @@ typedef struct {
   int32_t rows_per_lane;
   int32_t fuse;
   int32_t overlap;
+  int32_t hybrid_min;
 } ddhf_tuning;
 
 const char *ddhf_status_string(ddhf_status s);

@@ -46,6 +46,7 @@ ddhf_status dev_alloc(Ctx *c, T **p, size_t count) {
 
 void free_all(Ctx *c) {
   slide_free(c);
+  hybrid_free(c);
   auto F = [](void *p) {
     if (p) cudaFree(p);
   };
@@ -353,7 +354,7 @@ ddhf_status ddhf_create(int32_t W, int32_t H, const ddhf_grid *grid, const ddhf_
   c->params = *params;
   c->max_events = max_events;
   c->max_windows = max_windows;
-  c->tuning = ddhf_tuning{1024, 4, 0, 0, 0, 0};
+  c->tuning = ddhf_tuning{1024, 4, 0, 0, 0, 0, 0};
   cudaError_t e = cudaGetDevice(&c->device);
   if (e == cudaSuccess)
     e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
@@ -450,9 +451,14 @@ ddhf_status ddhf_set_tuning(ddhf_ctx *h, const ddhf_tuning *t) {
                             t->warps_per_block != 8) ||
       t->blocks_per_sm < 0 || t->blocks_per_sm > 32 ||
       !(r == 0 || r == 1 || r == 2 || r == 4 || r == 6 || r == 8) ||
-      (t->fuse != 0 && t->fuse != 1) || (t->overlap != 0 && t->overlap != 1))
+      (t->fuse != 0 && t->fuse != 1) || (t->overlap != 0 && t->overlap != 1) ||
+      t->hybrid_min < 0)
     return fail(&h->c, DDHF_ERR_INVALID_ARG, "tuning out of range");
   Ctx *c = &h->c;
+  if (t->hybrid_min > 0) {
+    const ddhf_status hs = hybrid_alloc(c);
+    if (hs != DDHF_OK) return hs;
+  }
   if (t->overlap && c->pbuf && !c->pbuf2) {
     // second spectrum buffer, a stream and events for overlapped windows
     if (cudaMalloc(&c->pbuf2, (size_t)c->npx * c->pbuf_ld * sizeof(float)) != cudaSuccess) {

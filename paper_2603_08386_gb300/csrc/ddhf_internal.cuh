@@ -76,6 +76,18 @@ struct GridConst {
 
 struct SlideState;  // sliding-window spectra (slide.cu)
 
+// Hybrid spectra (ndft_hybrid.cu): the grid rows a window needs, at most
+// kHybMaxG, and the event-count threshold of the pixels that take the path.
+constexpr int kHybMaxG = 1024;
+constexpr int kHybDefaultMin = 64;  // DDHF_FORM_HYBRID when the tuning sets none
+struct HybridPlan {
+  bool ok = false;
+  int64_t s = 0;      // grid spacing (us)
+  int G = 0, Gp = 0;  // grid rows, rounded up to the K chunk
+  int64_t thr = 0;    // pixels with at least thr events
+  int64_t cap_h = 0;  // pixel capacity (column stride of the coefficient matrix)
+};
+
 struct Ctx {
   int W = 0, H = 0;
   int row0 = 0;  // sensor row of row 0 (a row band of a larger sensor)
@@ -140,6 +152,15 @@ struct Ctx {
   cudaGraphExec_t graph_exec = nullptr;
   std::vector<uint8_t> graph_key;
   SlideState *slide = nullptr;  // ddhf_slide_begin .. ddhf_slide_end
+  // hybrid spectra (allocated once tuning.hybrid_min > 0 or DDHF_FORM_HYBRID is used)
+  float4 *hyb_c = nullptr;       // [hyb_celems] grid coefficients (cr, ci, cr+ci, cr+ci)
+  int64_t hyb_celems = 0;
+  float2 *hyb_eri = nullptr;     // [kHybMaxG][hyb_np] table E of the grid product
+  float *hyb_es = nullptr;       // [kHybMaxG][hyb_np] Re E + Im E
+  float *hyb_dec = nullptr;      // [n_bins] deconvolution factors
+  uint32_t *hyb_list = nullptr;  // [hyb_list_cap] active indices of the window's hybrid pixels
+  int64_t hyb_list_cap = 0;
+  int64_t hyb_np = 0;            // n_bins rounded up to the bin tile (128)
 };
 
 // ---------------------------------------------------------------- helpers
@@ -220,6 +241,13 @@ ddhf_status launch_scan_u64(Ctx *c, const uint64_t *in, uint64_t *out, int64_t n
                             cudaStream_t s);
 // slide.cu
 void slide_free(Ctx *c);
+// ndft_hybrid.cu
+int64_t hybrid_spacing(const ddhf_grid &g);
+HybridPlan hybrid_plan(const Ctx *c, int64_t window_us, int hybrid_min);
+ddhf_status hybrid_alloc(Ctx *c);
+void hybrid_free(Ctx *c);
+ddhf_status launch_hybrid(Ctx *c, int slot, const HybridPlan &hp, float *P, int64_t cap_px,
+                          int64_t ld, cudaStream_t s);
 // ndft.cu
 ddhf_status launch_spectrum(Ctx *c, int form, float *P, int64_t cap_px, cudaStream_t s);
 ddhf_status launch_spectrum_slot(Ctx *c, int slot, float *P, int64_t cap_px, cudaStream_t s,

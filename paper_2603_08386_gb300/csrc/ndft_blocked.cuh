@@ -234,6 +234,8 @@ struct BlockedArgs {
   int vec_store;             // P and ld 16-byte aligned
   int64_t cap_px;
   int heavy_min;
+  int skip_min;              // > 0: pixels with at least this many events are left to the
+                             // hybrid grid path (their rows are written there)
   int warp_bytes;            // per-warp shared memory (bytes)
   int pw_offset;             // byte offset of the spectrum buffer inside a warp's area
   uint32_t *flags;
@@ -317,6 +319,7 @@ __global__ void k_blocked(BlockedArgs A) {
     const uint32_t key = v.active[a];
     const uint32_t o0 = v.offsets[key];
     const int cnt = (int)(v.offsets[key + 1] - o0);
+    if (A.skip_min > 0 && cnt >= A.skip_min) continue;
     const int rows_per_pass = 4 * TB;
     bool overflow = !FUSED && a >= A.cap_px;
     if (overflow) {
@@ -409,6 +412,7 @@ __global__ void k_blocked(BlockedArgs A) {
       const uint32_t *evp = reinterpret_cast<const uint32_t *>(
           __shfl_sync(0xffffffffu, reinterpret_cast<uintptr_t>(m_ev), q));
       if (cnt < 0 || cnt >= A.heavy_min) continue;  // inactive, past the end, or heavy
+      if (A.skip_min > 0 && cnt >= A.skip_min) continue;  // hybrid grid path
       if (!FUSED && a >= A.cap_px) {
         if (lane == 0) raise_flag(A.flags, DDHF_FLAG_CAPACITY);
         continue;
@@ -447,7 +451,7 @@ int blocked_warp_bytes(const Ctx *c, bool fused, int NW, int *pw_offset) {
 
 template <int TB, int NW, bool FUSED>
 ddhf_status launch_blocked_t(Ctx *c, int n_slots, float *P, int64_t cap_px, cudaStream_t s,
-                             int slot0 = 0, int64_t ld = 0) {
+                             int slot0 = 0, int64_t ld = 0, int skip_min = 0) {
   BlockedArgs A{};
   A.views = c->d_views;
   A.slot0 = slot0;
@@ -464,6 +468,7 @@ ddhf_status launch_blocked_t(Ctx *c, int n_slots, float *P, int64_t cap_px, cuda
   A.vec_store = (A.ld % 4 == 0) && (reinterpret_cast<uintptr_t>(P) % 16 == 0);
   A.cap_px = cap_px;
   A.heavy_min = c->tuning.heavy_min;
+  A.skip_min = skip_min;
   A.warp_bytes = blocked_warp_bytes<TB>(c, FUSED, NW, &A.pw_offset);
   A.flags = c->flags;
   const int wpb = c->tuning.warps_per_block;
@@ -487,17 +492,22 @@ ddhf_status launch_blocked_t(Ctx *c, int n_slots, float *P, int64_t cap_px, cuda
 // One kernel instantiation per rows-per-lane choice TB, for comb variant NW.
 template <int NW, bool FUSED>
 ddhf_status launch_blocked_tb(Ctx *c, int n_slots, float *P, int64_t cap_px, cudaStream_t s,
-                              int slot0, int64_t ld) {
+                              int slot0, int64_t ld, int skip_min) {
   const int nbr = c->gconst.nbr;
   int tb = std::min(8, (nbr + 3) / 4);
   tb = tb <= 2 ? tb : tb <= 4 ? 4 : tb <= 6 ? 6 : 8;
   if (c->tuning.rows_per_lane > 0) tb = c->tuning.rows_per_lane;
   switch (tb) {
-    case 1: return launch_blocked_t<1, NW, FUSED>(c, n_slots, P, cap_px, s, slot0, ld);
-    case 2: return launch_blocked_t<2, NW, FUSED>(c, n_slots, P, cap_px, s, slot0, ld);
-    case 4: return launch_blocked_t<4, NW, FUSED>(c, n_slots, P, cap_px, s, slot0, ld);
-    case 6: return launch_blocked_t<6, NW, FUSED>(c, n_slots, P, cap_px, s, slot0, ld);
-    case 8: return launch_blocked_t<8, NW, FUSED>(c, n_slots, P, cap_px, s, slot0, ld);
+    case 1: return launch_blocked_t<1, NW, FUSED>(c, n_slots, P, cap_px, s, slot0, ld,
+                                                    skip_min);
+    case 2: return launch_blocked_t<2, NW, FUSED>(c, n_slots, P, cap_px, s, slot0, ld,
+                                                    skip_min);
+    case 4: return launch_blocked_t<4, NW, FUSED>(c, n_slots, P, cap_px, s, slot0, ld,
+                                                    skip_min);
+    case 6: return launch_blocked_t<6, NW, FUSED>(c, n_slots, P, cap_px, s, slot0, ld,
+                                                    skip_min);
+    case 8: return launch_blocked_t<8, NW, FUSED>(c, n_slots, P, cap_px, s, slot0, ld,
+                                                    skip_min);
   }
   return DDHF_ERR_UNSUPPORTED;
 }
@@ -505,21 +515,21 @@ ddhf_status launch_blocked_tb(Ctx *c, int n_slots, float *P, int64_t cap_px, cud
 // The fused kernels with the generic comb (1 or 8 mask words) are
 // instantiated in their own translation unit.
 extern template ddhf_status launch_blocked_tb<1, true>(Ctx *, int, float *, int64_t, cudaStream_t,
-                                                       int, int64_t);
+                                                       int, int64_t, int);
 extern template ddhf_status launch_blocked_tb<8, true>(Ctx *, int, float *, int64_t, cudaStream_t,
-                                                       int, int64_t);
+                                                       int, int64_t, int);
 
 template <bool FUSED>
 ddhf_status launch_blocked_any(Ctx *c, int n_slots, float *P, int64_t cap_px, cudaStream_t s,
-                               int slot0 = 0, int64_t ld = 0) {
+                               int slot0 = 0, int64_t ld = 0, int skip_min = 0) {
   if constexpr (!FUSED) {
-    return launch_blocked_tb<1, false>(c, n_slots, P, cap_px, s, slot0, ld);
+    return launch_blocked_tb<1, false>(c, n_slots, P, cap_px, s, slot0, ld, skip_min);
   } else {
     // the comb variant of the spectrum size: fast, or generic with 1 or 8 mask words
     switch (comb_variant(c->comb)) {
-      case 0: return launch_blocked_tb<0, true>(c, n_slots, P, cap_px, s, slot0, ld);
-      case 1: return launch_blocked_tb<1, true>(c, n_slots, P, cap_px, s, slot0, ld);
-      default: return launch_blocked_tb<8, true>(c, n_slots, P, cap_px, s, slot0, ld);
+      case 0: return launch_blocked_tb<0, true>(c, n_slots, P, cap_px, s, slot0, ld, 0);
+      case 1: return launch_blocked_tb<1, true>(c, n_slots, P, cap_px, s, slot0, ld, 0);
+      default: return launch_blocked_tb<8, true>(c, n_slots, P, cap_px, s, slot0, ld, 0);
     }
   }
 }

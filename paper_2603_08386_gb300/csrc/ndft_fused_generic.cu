@@ -6,8 +6,8 @@
 namespace ddhf {
 namespace blocked {
 template ddhf_status launch_blocked_tb<1, true>(Ctx *, int, float *, int64_t, cudaStream_t, int,
-                                                int64_t);
+                                                int64_t, int);
 template ddhf_status launch_blocked_tb<8, true>(Ctx *, int, float *, int64_t, cudaStream_t, int,
-                                                int64_t);
+                                                int64_t, int);
 }  // namespace blocked
 }  // namespace ddhf

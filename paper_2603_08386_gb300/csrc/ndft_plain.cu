@@ -14,6 +14,7 @@
 namespace ddhf {
 
 ddhf_status launch_blocked_spectrum(Ctx *c, float *P, int64_t cap_px, cudaStream_t s);
+ddhf_status launch_hybrid_spectrum(Ctx *c, float *P, int64_t cap_px, cudaStream_t s);
 
 namespace {
 
@@ -164,6 +165,7 @@ ddhf_status launch_spectrum(Ctx *c, int form, float *P, int64_t cap_px, cudaStre
     case DDHF_FORM_KAHAN: return launch_plain_form<DDHF_FORM_KAHAN>(c, P, cap_px, s);
     case DDHF_FORM_F64: return launch_plain_form<DDHF_FORM_F64>(c, P, cap_px, s);
     case DDHF_FORM_BLOCKED: return launch_blocked_spectrum(c, P, cap_px, s);
+    case DDHF_FORM_HYBRID: return launch_hybrid_spectrum(c, P, cap_px, s);
     default:
       c->last_error = "unknown NDFT form";
       return DDHF_ERR_INVALID_ARG;

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libddhf.so")
 DDHF_OK = 0
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "CAPACITY", 4: "TIMEOUT", 5: "UNSUPPORTED",
           6: "STATE"}
-FORM = dict(sincos=0, recur=1, blocked=2, naive32=3, kahan=4, f64=5)
+FORM = dict(sincos=0, recur=1, blocked=2, naive32=3, kahan=4, f64=5, hybrid=6)
 FLAG_CAPACITY, FLAG_TIMEOUT = 1, 2
 
 
@@ -64,7 +64,8 @@ class ddhf_stats(ctypes.Structure):
 class ddhf_tuning(ctypes.Structure):
     _fields_ = [("heavy_min", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("rows_per_lane", ctypes.c_int32),
-                ("fuse", ctypes.c_int32), ("overlap", ctypes.c_int32)]
+                ("fuse", ctypes.c_int32), ("overlap", ctypes.c_int32),
+                ("hybrid_min", ctypes.c_int32)]
 
 
 class ddhf_component(ctypes.Structure):
@@ -199,9 +200,9 @@ def ddhf_destroy(ctx):
 
 
 def ddhf_set_tuning(ctx, heavy_min=1024, warps_per_block=4, blocks_per_sm=0, rows_per_lane=0,
-                    fuse=0, overlap=0):
+                    fuse=0, overlap=0, hybrid_min=0):
     t = ddhf_tuning(int(heavy_min), int(warps_per_block), int(blocks_per_sm), int(rows_per_lane),
-                    int(fuse), int(overlap))
+                    int(fuse), int(overlap), int(hybrid_min))
     _check(load().ddhf_set_tuning(ctx, ctypes.byref(t)), ctx)
 
 
@@ -214,7 +215,7 @@ def ddhf_get_tuning(ctx):
     _check(load().ddhf_get_tuning(ctx, ctypes.byref(t)), ctx)
     return dict(heavy_min=t.heavy_min, warps_per_block=t.warps_per_block,
                 blocks_per_sm=t.blocks_per_sm, rows_per_lane=t.rows_per_lane, fuse=t.fuse,
-                overlap=t.overlap)
+                overlap=t.overlap, hybrid_min=t.hybrid_min)
 
 
 def ddhf_bin_events(ctx, x, y, t, p, n, t0, window_us, stream=None):

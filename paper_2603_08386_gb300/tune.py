@@ -2,7 +2,8 @@
 
 Times ``ddhf_detect_batch`` on the caller's own windows for each candidate
 ``ddhf_tuning`` (heavy-pixel threshold, warps per block, rows per lane, fused
-or separate spectrum and comb kernels, overlapped windows) by the wall time
+or separate spectrum and comb kernels, overlapped windows, the event count
+from which pixels take the hybrid grid route) by the wall time
 of the whole call (CUDA events on its stream), keeps the fastest, sets it on
 the context, and caches the choice in a JSON file keyed by device, sensor,
 grid, parameters and workload shape, so later runs reuse it without timing. Only the launch configuration changes; every
@@ -25,11 +26,13 @@ DEFAULT_CANDIDATES = [
     for wpb in (4, 8)
     for r in (0, 4)
 ] + [
-    dict(heavy_min=hm, warps_per_block=wpb, blocks_per_sm=0, rows_per_lane=r, fuse=0, overlap=ov)
-    for hm in (128, 256, 512, 1024, 4096)
+    dict(heavy_min=hm, warps_per_block=wpb, blocks_per_sm=0, rows_per_lane=r, fuse=0, overlap=ov,
+         hybrid_min=hy)
+    for hm in (128, 256, 1024, 4096)
     for wpb in (4, 8)
     for r in (0, 4)
     for ov in (0, 1)
+    for hy in (0, 64, 128, 256)
 ]
 
 

@@ -50,8 +50,12 @@ def test_search_beats_table2_on_held_out_windows():
     test = evaluate.Evaluator([synth.labelled_scene(400 + i) for i in range(4)])
     t2 = ddhf.default_params()
     f_t2 = test.f1(t2)
-    best, f_val, hist = evaluate.tune(val, n_init=16, n_iter=24, seed=0)
-    assert len(hist) == 40
+    # 30 uniformly random points, then 90 expected-improvement steps (one
+    # detection of each validation window per evaluation); the F1 surface is
+    # flat almost everywhere, so the budget has to reach the narrow region
+    # where drones and noise separate
+    best, f_val, hist = evaluate.tune(val, n_init=30, n_iter=90, seed=0)
+    assert len(hist) == 120
     f_test = test.f1(evaluate.params_of(best))
     print(f"Table 2 F1 {f_t2:.3f}; tuned {best} val F1 {f_val:.3f} test F1 {f_test:.3f}")
     assert f_val >= 0.8
