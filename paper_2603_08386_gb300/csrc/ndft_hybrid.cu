@@ -50,14 +50,32 @@ constexpr int kCopies = 32 / kW;  // event groups per warp step
 constexpr int kCopyPad = 8;       // float2 between grid copies: the four groups of a
                                   // step fall on alternate halves of the banks
 
+constexpr uint32_t kFrontMin = 1024;  // pixels listed first (taken first by the spread)
+
+// The kernel in grid steps z, |z| <= w / 2, from the hardware reciprocal
+// square root and base-2 exponential (relative error a few 1e-7 at the
+// largest exponent, beta; the route's own error is ~1e-7 of the peak power).
 __device__ __forceinline__ float es_kernel(float z) {
-  // z in grid steps, |z| <= w / 2
   const float x = __fmul_rn(z, 2.0f / kW);
   const float r = fmaxf(__fsub_rn(1.0f, __fmul_rn(x, x)), 0.0f);
-  return expf((float)kBeta * (sqrtf(r) - 1.0f));
+  const float sq = r > 0.0f ? __fmul_rn(r, rsqrtf(r)) : 0.0f;
+  return __expf((float)kBeta * (sq - 1.0f));
 }
 
-// Active indices a of the slot's pixels with at least thr events.
+// Entry h of the hybrid list: pixels with at least kFrontMin events are
+// stored from the front (count[0] of them), the others from the back.
+__device__ __forceinline__ uint32_t list_at(const uint32_t *list, const uint32_t *count,
+                                            int64_t cap, int64_t h) {
+  const uint32_t nf = count[0];
+  return h < (int64_t)nf ? list[h] : list[cap - 1 - (h - (int64_t)nf)];
+}
+
+__device__ __forceinline__ int64_t list_size(const uint32_t *count, int64_t cap) {
+  return min((int64_t)count[0] + (int64_t)count[1], cap);
+}
+
+// Active indices a of the slot's pixels with at least thr events, the
+// heaviest (>= kFrontMin) at the front so that they are spread first.
 __global__ void k_hyb_list(const uint32_t *__restrict__ active, const uint32_t *__restrict__ offsets,
                            const uint64_t *__restrict__ counters, int thr, uint32_t *list,
                            uint32_t *count, int64_t cap, uint32_t *flags) {
@@ -66,19 +84,25 @@ __global__ void k_hyb_list(const uint32_t *__restrict__ active, const uint32_t *
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n_act;
        base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t a = base + threadIdx.x;
-    bool take = false;
+    uint32_t cnt = 0;
     if (a < n_act) {
       const uint32_t k = active[a];
-      take = offsets[k + 1] - offsets[k] >= (uint32_t)thr;
+      cnt = offsets[k + 1] - offsets[k];
     }
-    const uint32_t bal = __ballot_sync(0xffffffffu, take);
-    uint32_t pos0 = 0;
-    if (lane == 0 && bal) pos0 = atomicAdd(count, (uint32_t)__popc(bal));
-    pos0 = __shfl_sync(0xffffffffu, pos0, 0);
-    if (take) {
-      const uint32_t pos = pos0 + __popc(bal & ((1u << lane) - 1u));
-      if ((int64_t)pos < cap) list[pos] = (uint32_t)a;
-      else atomicOr(flags, DDHF_FLAG_INTERNAL);
+    const bool take = a < n_act && cnt >= (uint32_t)thr;
+    const bool front = take && cnt >= kFrontMin;
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const bool mine = side == 0 ? front : (take && !front);
+      const uint32_t bal = __ballot_sync(0xffffffffu, mine);
+      uint32_t pos0 = 0;
+      if (lane == 0 && bal) pos0 = atomicAdd(count + side, (uint32_t)__popc(bal));
+      pos0 = __shfl_sync(0xffffffffu, pos0, 0);
+      if (mine) {
+        const int64_t pos = pos0 + __popc(bal & ((1u << lane) - 1u));
+        if (pos < cap) list[side == 0 ? pos : cap - 1 - pos] = (uint32_t)a;
+        else atomicOr(flags, DDHF_FLAG_INTERNAL);
+      }
     }
   }
 }
@@ -144,7 +168,7 @@ __global__ void __launch_bounds__(kSpreadWarps * 32) k_hyb_spread(SpreadArgs A) 
   float2 *acc = sm2 + (int64_t)warp * kCopies * cs;
   const int ncopy = nw * kCopies;
   // the list holds at most cap_h entries (an overflow raised DDHF_FLAG_INTERNAL)
-  const uint32_t n_h = (uint32_t)min((int64_t)*A.count, A.cap_h);
+  const uint32_t n_h = (uint32_t)list_size(A.count, A.cap_h);
   const int grp = lane / kW, ii = lane % kW;
   constexpr int kSteps = 32 / kCopies;
   for (int i = threadIdx.x; i < ncopy * cs; i += blockDim.x) sm2[i] = make_float2(0.f, 0.f);
@@ -154,7 +178,7 @@ __global__ void __launch_bounds__(kSpreadWarps * 32) k_hyb_spread(SpreadArgs A) 
     const uint32_t h = s_item;
     __syncthreads();
     if (h >= n_h) break;
-    const uint32_t a = A.list[h];
+    const uint32_t a = list_at(A.list, A.count, A.cap_h, h);
     const uint32_t key = A.active[a];
     const uint32_t p0 = A.offsets[key], p1 = A.offsets[key + 1];
     const uint32_t n = p1 - p0;
@@ -276,7 +300,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_hyb_grid(GridArgs A) {
   extern __shared__ float4 gsm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int ty = warp * 2 + (lane >> 4), tx = lane & 15;
-  const int64_t n_h = min((int64_t)*A.count, A.cap_h);
+  const int64_t n_h = list_size(A.count, A.cap_h);
   const int nbt = A.np / kTileB;
   const int64_t n_tiles = ((n_h + kTileP - 1) / kTileP) * nbt;
   const int nk = A.Gp / kKC;
@@ -331,7 +355,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_hyb_grid(GridArgs A) {
     for (int p = 0; p < 4; ++p) {
       const int64_t h = p0 + 4 * ty + p;
       if (h >= n_h) continue;
-      const int64_t a = (int64_t)A.list[h];
+      const int64_t a = (int64_t)list_at(A.list, A.count, A.cap_h, h);
       if (a >= A.cap_px) {
         atomicOr(A.flags, DDHF_FLAG_CAPACITY);
         continue;
@@ -453,8 +477,8 @@ void hybrid_free(Ctx *c) {
 ddhf_status launch_hybrid(Ctx *c, int slot, const HybridPlan &hp, float *P, int64_t cap_px,
                           int64_t ld, cudaStream_t s) {
   const Slot &sl = c->slots[slot];
-  uint32_t *count = c->qctl + 12;
-  DDHF_CUDA_TRY(c, cudaMemsetAsync(count, 0, sizeof(uint32_t), s));
+  uint32_t *count = c->qctl + 12;  // [0] front (heaviest), [1] back
+  DDHF_CUDA_TRY(c, cudaMemsetAsync(count, 0, 2 * sizeof(uint32_t), s));
   k_hyb_list<<<c->num_sms * 8, 256, 0, s>>>(sl.active, sl.offsets, sl.counters, (int)hp.thr,
                                             c->hyb_list, count, hp.cap_h, c->flags);
   DDHF_CUDA_TRY(c, cudaGetLastError());
@@ -485,7 +509,7 @@ ddhf_status launch_hybrid(Ctx *c, int slot, const HybridPlan &hp, float *P, int6
   S.Gp = hp.Gp;
   S.cap_h = hp.cap_h;
   S.C = c->hyb_c;
-  S.cursor = c->qctl + 13;
+  S.cursor = c->qctl + 14;
   DDHF_CUDA_TRY(c, cudaMemsetAsync(S.cursor, 0, sizeof(uint32_t), s));
   // warps per pixel: up to 8, with their grid copies within 192 KiB
   const int cs = hp.Gp + kCopyPad;
