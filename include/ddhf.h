@@ -142,8 +142,9 @@ typedef struct {
  *           semicircle" kernel of 8 points (Barnett et al. 2019), and the
  *           grid's G = (window_us - 1) / s + 8 values enter one dense complex
  *           product with a table shared by all pixels, deconvolved per bin.
- *           Within about 1e-6 of the exact Eq. 6 power relative to the
- *           pixel's peak. A window with G < 16 or G > 1024 (or a grid with
+ *           Within a few 1e-6 of the exact Eq. 6 power relative to the
+ *           pixel's peak (FP32 sums and hardware exp2 / rsqrt in the
+ *           kernel values). A window with G < 16 or G > 1024 (or a grid with
  *           s < 1) runs BLOCKED alone. The first use allocates the path's
  *           workspace (about 64 bytes per max_events plus 12 KiB per bin). */
 #define DDHF_FORM_SINCOS 0

@@ -66,3 +66,18 @@ def test_bad_arguments_rejected_without_gpu():
     assert lib.ddhf_create(10, 10, ctypes.byref(g), ctypes.byref(p), 10, 1, ctypes.byref(h)) == 5
     assert lib.ddhf_bin_events(None, None, None, None, None, 0, 0, 1, None) == 1
     assert lib.ddhf_status_string(3) == b"capacity exceeded"
+
+
+def test_binding_forms_and_tuning_match_header():
+    # the DDHF_FORM_* numbers and the ddhf_tuning fields of the header are
+    # the ones the binding marshals
+    import ctypes as ct
+    from paper_2603_08386_gb300 import ddhf
+    src = open(os.path.join(ROOT, "include", "ddhf.h")).read()
+    forms = {m.group(1).lower(): int(m.group(2))
+             for m in re.finditer(r"#define DDHF_FORM_(\w+) (\d+)", src)}
+    assert forms == ddhf.FORM
+    body = re.search(r"typedef struct \{([^}]*)\} ddhf_tuning;", src).group(1)
+    fields = re.findall(r"int32_t (\w+);", body)
+    assert fields == [f for f, _ in ddhf.ddhf_tuning._fields_]
+    assert ct.sizeof(ddhf.ddhf_tuning) == 4 * len(fields)
