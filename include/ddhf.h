@@ -221,6 +221,16 @@ ddhf_status ddhf_set_tuning(ddhf_ctx *ctx, const ddhf_tuning *tuning);
 ddhf_status ddhf_set_params(ddhf_ctx *ctx, const ddhf_params *params);
 ddhf_status ddhf_get_tuning(const ddhf_ctx *ctx, ddhf_tuning *out);
 
+/* Iteration limit of the context's bounded device-side loops (the
+ * union-find walks of labelling and of the Eq. 12 merge; default 2^24,
+ * which no valid input reaches). A loop that reaches the limit stops,
+ * raises DDHF_FLAG_TIMEOUT (ddhf_get_stats then returns DDHF_ERR_TIMEOUT and
+ * clears it) and leaves in-range but unreliable labels or boxes; the context
+ * stays usable. Not in the paper: this is how a test drives the timeout path
+ * without stalling the GPU. limit >= 1; a cached ddhf_detect_batch graph is
+ * dropped. */
+ddhf_status ddhf_set_loop_limit(ddhf_ctx *ctx, int32_t limit);
+
 /* Sec. 3.5 "Event processing": keep events with t0 <= t < t0+window_us,
  * 0 <= x < W, 0 <= y < H and a valid polarity, sort them stably by pixel key
  * y*W + x into the context's per-pixel list (slot 0), and list the active

@@ -478,6 +478,14 @@ ddhf_status ddhf_set_tuning(ddhf_ctx *h, const ddhf_tuning *t) {
   return DDHF_OK;
 }
 
+ddhf_status ddhf_set_loop_limit(ddhf_ctx *h, int32_t limit) {
+  if (!h) return DDHF_ERR_INVALID_ARG;
+  if (limit < 1) return fail(&h->c, DDHF_ERR_INVALID_ARG, "loop limit < 1");
+  h->c.loop_limit = limit;
+  drop_graph(&h->c);
+  return DDHF_OK;
+}
+
 ddhf_status ddhf_enable_stage_timing(ddhf_ctx *h, int32_t enable) {
   if (!h) return DDHF_ERR_INVALID_ARG;
   Ctx *c = &h->c;

@@ -19,9 +19,11 @@ namespace ddhf {
 
 namespace {
 
-constexpr int kFindLimit = 1 << 24;
-
-__device__ __forceinline__ int find_root(int32_t *lab, int x, uint32_t *flags) {
+// Every union-find loop below stops after `limit` iterations (the context's
+// loop limit, 2^24 unless a test lowers it), raises DDHF_FLAG_TIMEOUT and
+// returns an index that is still in range, so a run-out leaves wrong labels
+// but no bad access.
+__device__ __forceinline__ int find_root(int32_t *lab, int x, uint32_t *flags, int limit) {
   int it = 0;
   int p = lab[x];
   while (p != x) {
@@ -29,7 +31,7 @@ __device__ __forceinline__ int find_root(int32_t *lab, int x, uint32_t *flags) {
     if (gp < p) lab[x] = gp;  // path halving; parents only move to smaller ancestors
     x = p;
     p = gp;
-    if (++it > kFindLimit) {
+    if (++it > limit) {
       atomicOr(flags, DDHF_FLAG_TIMEOUT);
       break;
     }
@@ -37,10 +39,10 @@ __device__ __forceinline__ int find_root(int32_t *lab, int x, uint32_t *flags) {
   return x;
 }
 
-__device__ __forceinline__ void unite(int32_t *lab, int a, int b, uint32_t *flags) {
-  for (int it = 0; it < kFindLimit; ++it) {
-    a = find_root(lab, a, flags);
-    b = find_root(lab, b, flags);
+__device__ __forceinline__ void unite(int32_t *lab, int a, int b, uint32_t *flags, int limit) {
+  for (int it = 0; it < limit; ++it) {
+    a = find_root(lab, a, flags, limit);
+    b = find_root(lab, b, flags, limit);
     if (a == b) return;
     if (a < b) {
       int t = a;
@@ -66,18 +68,18 @@ __global__ void k_label_init(const uint8_t *__restrict__ mask, int32_t *__restri
 }
 
 __global__ void k_label_union(const uint8_t *__restrict__ mask, int32_t *lab, int W, int H,
-                              uint32_t *flags) {
+                              uint32_t *flags, int limit) {
   const int64_t npx = (int64_t)W * H;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npx;
        i += (int64_t)gridDim.x * blockDim.x) {
     if (!mask[i]) continue;
     const int x = (int)(i % W), y = (int)(i / W);
-    if (x > 0 && mask[i - 1]) unite(lab, (int)i, (int)(i - 1), flags);
+    if (x > 0 && mask[i - 1]) unite(lab, (int)i, (int)(i - 1), flags, limit);
     if (y > 0) {
       const int64_t up = i - W;
-      if (x > 0 && mask[up - 1]) unite(lab, (int)i, (int)(up - 1), flags);
-      if (mask[up]) unite(lab, (int)i, (int)up, flags);
-      if (x < W - 1 && mask[up + 1]) unite(lab, (int)i, (int)(up + 1), flags);
+      if (x > 0 && mask[up - 1]) unite(lab, (int)i, (int)(up - 1), flags, limit);
+      if (mask[up]) unite(lab, (int)i, (int)up, flags, limit);
+      if (x < W - 1 && mask[up + 1]) unite(lab, (int)i, (int)(up + 1), flags, limit);
     }
   }
 }
@@ -85,8 +87,9 @@ __global__ void k_label_union(const uint8_t *__restrict__ mask, int32_t *lab, in
 // Root of x without writing any parent: during the compress pass every thread
 // writes only its own pixel, so no stale path-halving write can overwrite a
 // root that another thread has already stored.
-__device__ __forceinline__ int find_root_ro(const int32_t *lab, int x, uint32_t *flags) {
-  for (int it = 0; it < kFindLimit; ++it) {
+__device__ __forceinline__ int find_root_ro(const int32_t *lab, int x, uint32_t *flags,
+                                            int limit) {
+  for (int it = 0; it < limit; ++it) {
     const int p = lab[x];
     if (p == x) return x;
     x = p;
@@ -95,10 +98,10 @@ __device__ __forceinline__ int find_root_ro(const int32_t *lab, int x, uint32_t 
   return x;
 }
 
-__global__ void k_label_compress(int32_t *lab, int64_t npx, uint32_t *flags) {
+__global__ void k_label_compress(int32_t *lab, int64_t npx, uint32_t *flags, int limit) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npx;
        i += (int64_t)gridDim.x * blockDim.x) {
-    if (lab[i] >= 0) lab[i] = find_root_ro(lab, (int)i, flags);
+    if (lab[i] >= 0) lab[i] = find_root_ro(lab, (int)i, flags, limit);
   }
 }
 
@@ -191,14 +194,14 @@ __device__ __forceinline__ bool eq12_close(const int32_t *a, const int32_t *b, d
   return lhs < __dmul_rn(s, s);
 }
 
-__device__ __forceinline__ int gfind(int32_t *par, int x, uint32_t *flags) {
+__device__ __forceinline__ int gfind(int32_t *par, int x, uint32_t *flags, int limit) {
   int p = par[x];
   for (int it = 0; p != x; ++it) {
     int gp = par[p];
     par[x] = gp;
     x = p;
     p = gp;
-    if (it > kFindLimit) {
+    if (it > limit) {
       atomicOr(flags, DDHF_FLAG_TIMEOUT);
       break;
     }
@@ -206,10 +209,10 @@ __device__ __forceinline__ int gfind(int32_t *par, int x, uint32_t *flags) {
   return x;
 }
 
-__device__ __forceinline__ void gunite(int32_t *par, int a, int b, uint32_t *flags) {
-  for (int it = 0; it < kFindLimit; ++it) {
-    a = gfind(par, a, flags);
-    b = gfind(par, b, flags);
+__device__ __forceinline__ void gunite(int32_t *par, int a, int b, uint32_t *flags, int limit) {
+  for (int it = 0; it < limit; ++it) {
+    a = gfind(par, a, flags, limit);
+    b = gfind(par, b, flags, limit);
     if (a == b) return;
     if (a < b) {
       int t = a;
@@ -235,7 +238,8 @@ __global__ void __launch_bounds__(kMergeThreads) k_box_merge(int32_t *list, int3
                                                              int32_t *par, int32_t *root,
                                                              const uint32_t *count,
                                                              double alpha, ddhf_box *out, int cap,
-                                                             int32_t *n_out, uint32_t *flags) {
+                                                             int32_t *n_out, uint32_t *flags,
+                                                             int limit) {
   __shared__ int any;
   __shared__ uint32_t warp_tot[32];
   __shared__ uint32_t s_base;
@@ -251,7 +255,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_box_merge(int32_t *list, int3
       if (j <= i) continue;
       if (eq12_close(list + 5 * (int64_t)i, list + 5 * (int64_t)j, alpha)) {
         any = 1;
-        gunite(par, i, j, flags);
+        gunite(par, i, j, flags, limit);
       }
     }
     __syncthreads();
@@ -260,7 +264,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_box_merge(int32_t *list, int3
       if (tid == 0) atomicOr(flags, DDHF_FLAG_TIMEOUT);
       break;
     }
-    for (int i = tid; i < B; i += bs) root[i] = find_root_ro(par, i, flags);
+    for (int i = tid; i < B; i += bs) root[i] = find_root_ro(par, i, flags, limit);
     __syncthreads();
     for (int i = tid; i < B; i += bs) par[i] = root[i];
     __syncthreads();
@@ -346,8 +350,8 @@ ddhf_status launch_label(Ctx *c, const uint8_t *mask, int32_t *labels, uint64_t 
   const int blocks = c->num_sms * 8;
   DDHF_CUDA_TRY(c, cudaMemsetAsync(nfg, 0, sizeof(uint64_t), s));
   k_label_init<<<blocks, 256, 0, s>>>(mask, labels, c->npx, nfg);
-  k_label_union<<<blocks, 256, 0, s>>>(mask, labels, c->W, c->H, c->flags);
-  k_label_compress<<<blocks, 256, 0, s>>>(labels, c->npx, c->flags);
+  k_label_union<<<blocks, 256, 0, s>>>(mask, labels, c->W, c->H, c->flags, c->loop_limit);
+  k_label_compress<<<blocks, 256, 0, s>>>(labels, c->npx, c->flags, c->loop_limit);
   DDHF_CUDA_TRY(c, cudaGetLastError());
   return DDHF_OK;
 }
@@ -380,7 +384,7 @@ ddhf_status launch_boxes(Ctx *c, const int32_t *labels, ddhf_box *boxes, int32_t
   k_box_accum<<<blocks, 256, 0, s>>>(labels, bx, c->W, npx);
   k_box_collect<<<blocks, 256, 0, s>>>(labels, bx, npx, c->params.A_min, list, count);
   k_box_merge<<<1, kMergeThreads, 0, s>>>(list, list2, par, bx, count, c->params.alpha, boxes,
-                                          cap, n_boxes, c->flags);
+                                          cap, n_boxes, c->flags, c->loop_limit);
   DDHF_CUDA_TRY(c, cudaGetLastError());
   return DDHF_OK;
 }

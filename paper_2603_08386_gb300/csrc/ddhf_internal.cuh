@@ -152,6 +152,7 @@ struct Ctx {
   cudaGraphExec_t graph_exec = nullptr;
   std::vector<uint8_t> graph_key;
   SlideState *slide = nullptr;  // ddhf_slide_begin .. ddhf_slide_end
+  int loop_limit = 1 << 24;     // iterations of the bounded device loops (ddhf_set_loop_limit)
   // hybrid spectra (allocated once tuning.hybrid_min > 0 or DDHF_FORM_HYBRID is used)
   float4 *hyb_c = nullptr;       // [hyb_celems] grid coefficients (cr, ci, cr+ci, cr+ci)
   int64_t hyb_celems = 0;

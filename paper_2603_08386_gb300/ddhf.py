@@ -92,6 +92,7 @@ SIGNATURES = {
     "ddhf_destroy": (_I32, [_VP]),
     "ddhf_set_tuning": (_I32, [_VP, ctypes.POINTER(ddhf_tuning)]),
     "ddhf_set_params": (_I32, [_VP, ctypes.POINTER(ddhf_params)]),
+    "ddhf_set_loop_limit": (_I32, [_VP, _I32]),
     "ddhf_get_tuning": (_I32, [_VP, ctypes.POINTER(ddhf_tuning)]),
     "ddhf_bin_events": (_I32, [_VP, _VP, _VP, _VP, _VP, _I64, _I64, _I64, _VP]),
     "ddhf_export_csr": (_I32, [_VP, _VP, _VP, _I64, _VP, _VP, _VP]),
@@ -208,6 +209,10 @@ def ddhf_set_tuning(ctx, heavy_min=1024, warps_per_block=4, blocks_per_sm=0, row
 
 def ddhf_set_params(ctx, params):
     _check(load().ddhf_set_params(ctx, ctypes.byref(params)), ctx)
+
+
+def ddhf_set_loop_limit(ctx, limit):
+    _check(load().ddhf_set_loop_limit(ctx, int(limit)), ctx)
 
 
 def ddhf_get_tuning(ctx):

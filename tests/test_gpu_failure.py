@@ -1,0 +1,71 @@
+"""Failure detection on the GPU without a GPU fault: the bounded union-find
+loops of labelling and of the Eq. 12 merge are made to run out (the
+context's loop limit lowered to 1), which must surface on the host as
+DDHF_ERR_TIMEOUT with DDHF_FLAG_TIMEOUT set, after which the same context
+(limit restored) labels the same mask exactly as the oracle does."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2603_08386_gb300 import ddhf, synth
+
+pytestmark = pytest.mark.gpu
+
+STATUS_TIMEOUT = 4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2603_08386_gb300 import build
+    build.build()
+    oracle.build()
+    ddhf.load()
+    assert torch.cuda.is_available()
+    yield
+
+
+def snake_mask(W, H):
+    # rows 1, 3, 5, ... filled and joined at alternating ends: one 8-connected
+    # component whose union-find paths are long
+    m = np.zeros((H, W), np.uint8)
+    for y in range(1, H - 1, 2):
+        m[y, 1:W - 1] = 1
+        if y + 2 < H - 1:
+            m[y + 1, (W - 2) if (y // 2) % 2 == 0 else 1] = 1
+    return m.reshape(-1)
+
+
+def test_loop_limit_runs_out_and_context_recovers():
+    W, H = 256, 40
+    c = ddhf.Context(W, H, synth.hz_grid(0, 2, 750), max_events=16)
+    m = snake_mask(W, H)
+    mask = torch.from_numpy(m).cuda()
+    ref, n_comp = oracle.ccl8(m, W, H)
+    assert n_comp == 1
+    bx = torch.empty((16, 5), dtype=torch.int32, device="cuda")
+    nb = torch.zeros(1, dtype=torch.int32, device="cuda")
+
+    ddhf.ddhf_set_loop_limit(c.h, 1)
+    lab = c.label(mask)
+    ddhf.ddhf_boxes(c.h, lab, bx, 16, nb)
+    st = c.stats(raise_on_flags=False)
+    assert st["status"] == STATUS_TIMEOUT
+    assert st["device_flags"] & 2  # DDHF_FLAG_TIMEOUT
+    # labels are unreliable after a run-out but stay in range
+    got = lab.cpu().numpy()
+    assert ((got == -1) | ((got >= 0) & (got < W * H))).all()
+
+    # the flags were cleared by the read; with the default limit the same
+    # context is exact again
+    ddhf.ddhf_set_loop_limit(c.h, 1 << 24)
+    lab = c.label(mask)
+    ddhf.ddhf_boxes(c.h, lab, bx, 16, nb)
+    st = c.stats(raise_on_flags=False)
+    assert st["status"] == 0 and st["device_flags"] == 0
+    np.testing.assert_array_equal(lab.cpu().numpy(), ref)
+    assert int(nb.item()) == 1
+    assert bx[0, :4].tolist() == [1, 1, W - 2, H - 2 - (H % 2 == 0)]
+    with pytest.raises(ddhf.DDHFError):
+        ddhf.ddhf_set_loop_limit(c.h, 0)
+    c.close()
