@@ -197,6 +197,22 @@ typedef struct {
 
 const char *ddhf_status_string(ddhf_status s);
 
+/* Host-only (no device, no context): how DDHF_FORM_HYBRID and the
+ * hybrid_min tuning treat a window of window_us on `grid` (host pointer).
+ * *s_us = floor(denom / (2 da n_bins)), the grid spacing in microseconds;
+ * *rows = (window_us - 1) / s + 8, the grid rows G; *threshold =
+ * max(hybrid_min, 16, ceil(G / 2)), the event count from which a pixel takes
+ * the route; dec[n_bins] (nullable; written when s >= 1) = the per-bin
+ * deconvolution factors 1 / psi^((j - floor(n_bins/2)) da s / denom) of the
+ * 8-point exponential-of-semicircle kernel. Returns DDHF_ERR_UNSUPPORTED
+ * (threshold 0) when the window runs BLOCKED alone (s < 1 or G outside
+ * [16, 1024]), DDHF_ERR_INVALID_ARG for a bad grid, window or hybrid_min < 1.
+ * The footnote to Sec. 3.3 names the route; its parameters are this
+ * library's. Any output pointer may be NULL. */
+ddhf_status ddhf_hybrid_geometry(const ddhf_grid *grid, int64_t window_us, int32_t hybrid_min,
+                                 int64_t *s_us, int32_t *rows, int32_t *threshold,
+                                 float *dec);
+
 /* Table 2 final values. out: host pointer. */
 ddhf_status ddhf_default_params(ddhf_params *out);
 

@@ -413,15 +413,38 @@ int64_t hybrid_spacing(const ddhf_grid &g) {
   return s >= 1.0 ? (int64_t)s : 0;
 }
 
+// Grid spacing, rows and pixel threshold of a window; false when the window
+// does not take the route (grid spacing below 1 us, or G outside [16, 1024]).
+// s and G are written either way.
+bool hybrid_geometry(const ddhf_grid &g, int64_t window_us, int hybrid_min, int64_t *s,
+                     int64_t *G, int64_t *thr) {
+  *s = hybrid_spacing(g);
+  *G = (*s >= 1 && window_us >= 1) ? (window_us - 1) / *s + kW : 0;
+  *thr = std::max<int64_t>(std::max(hybrid_min, 16), ceil_div(*G, 2));
+  return *s >= 1 && hybrid_min > 0 && window_us >= 1 && *G >= 16 && *G <= kHybMaxG;
+}
+
+// 1 / psi^(kappa_m) for the bins of grid g at spacing s: kappa_m = (j - J) da
+// s / D with J = floor(N / 2); psi^ is even, so one quadrature per |m|.
+void hybrid_dec_factors(const ddhf_grid &g, int64_t s, float *dec) {
+  const int N = g.n_bins, J = N / 2;
+  std::vector<float> by_abs_m(std::max(J, N - 1 - J) + 1);
+  for (size_t am = 0; am < by_abs_m.size(); ++am) {
+    const double kappa = (double)am * (double)g.da * (double)s / (double)g.denom;
+    by_abs_m[am] = (float)(1.0 / es_transform(kappa));
+  }
+  for (int j = 0; j < N; ++j) dec[j] = by_abs_m[std::abs(j - J)];
+}
+
 HybridPlan hybrid_plan(const Ctx *c, int64_t window_us, int hybrid_min) {
   HybridPlan p{};
-  p.s = hybrid_spacing(c->grid);
-  if (p.s < 1 || hybrid_min <= 0 || window_us < 1) return p;
-  const int64_t G = (window_us - 1) / p.s + kW;
-  if (G < 16 || G > kHybMaxG) return p;
+  int64_t G = 0;
+  if (!hybrid_geometry(c->grid, window_us, hybrid_min, &p.s, &G, &p.thr)) {
+    p.thr = 0;
+    return p;
+  }
   p.G = (int)G;
   p.Gp = (int)ceil_div(G, kKC) * kKC;
-  p.thr = std::max<int64_t>(std::max(hybrid_min, 16), ceil_div(G, 2));
   const int64_t cap = std::min<int64_t>(c->npx, c->max_events / p.thr + 1);
   p.cap_h = ceil_div(cap, kTileP) * kTileP;
   p.ok = (int64_t)p.Gp * p.cap_h <= c->hyb_celems && p.cap_h <= c->hyb_list_cap;
@@ -446,16 +469,8 @@ ddhf_status hybrid_alloc(Ctx *c) {
             al((void **)&c->hyb_dec, (size_t)N * sizeof(float)) &&
             al((void **)&c->hyb_list, (size_t)c->hyb_list_cap * sizeof(uint32_t));
   if (ok) {
-    // 1 / psi^(kappa_m), kappa_m = (j - J) da s / D; psi^ is even, so one
-    // quadrature per |m|
-    const int64_t s = hybrid_spacing(c->grid);
-    const int J = N / 2;
-    std::vector<float> dec(N), by_abs_m(std::max(J, N - 1 - J) + 1);
-    for (size_t am = 0; am < by_abs_m.size(); ++am) {
-      const double kappa = (double)am * (double)c->grid.da * (double)s / (double)c->grid.denom;
-      by_abs_m[am] = (float)(1.0 / es_transform(kappa));
-    }
-    for (int j = 0; j < N; ++j) dec[j] = by_abs_m[std::abs(j - J)];
+    std::vector<float> dec(N);
+    hybrid_dec_factors(c->grid, hybrid_spacing(c->grid), dec.data());
     ok = cudaMemcpy(c->hyb_dec, dec.data(), N * sizeof(float), cudaMemcpyHostToDevice) ==
          cudaSuccess;
     if (!ok) c->last_error = "hybrid: copy of the deconvolution factors failed";
@@ -553,3 +568,19 @@ ddhf_status launch_hybrid(Ctx *c, int slot, const HybridPlan &hp, float *P, int6
 }
 
 }  // namespace ddhf
+
+extern "C" ddhf_status ddhf_hybrid_geometry(const ddhf_grid *grid, int64_t window_us,
+                                            int32_t hybrid_min, int64_t *s_us, int32_t *rows,
+                                            int32_t *threshold, float *dec) {
+  if (!grid || grid->a0 < 0 || grid->da <= 0 || grid->denom <= 0 ||
+      grid->denom >= ((int64_t)1 << 31) || grid->n_bins < 1 || grid->n_bins > 16384 ||
+      window_us < 1 || window_us >= ((int64_t)1 << 31) || hybrid_min < 1)
+    return DDHF_ERR_INVALID_ARG;
+  int64_t s = 0, G = 0, thr = 0;
+  const bool ok = ddhf::hybrid_geometry(*grid, window_us, hybrid_min, &s, &G, &thr);
+  if (s_us) *s_us = s;
+  if (rows) *rows = (int32_t)std::min<int64_t>(G, INT32_MAX);
+  if (threshold) *threshold = ok ? (int32_t)thr : 0;
+  if (dec && s >= 1) ddhf::hybrid_dec_factors(*grid, s, dec);
+  return ok ? DDHF_OK : DDHF_ERR_UNSUPPORTED;
+}

@@ -93,6 +93,7 @@ SIGNATURES = {
     "ddhf_set_tuning": (_I32, [_VP, ctypes.POINTER(ddhf_tuning)]),
     "ddhf_set_params": (_I32, [_VP, ctypes.POINTER(ddhf_params)]),
     "ddhf_set_loop_limit": (_I32, [_VP, _I32]),
+    "ddhf_hybrid_geometry": (_I32, [ctypes.POINTER(ddhf_grid), _I64, _I32, _VP, _VP, _VP, _VP]),
     "ddhf_get_tuning": (_I32, [_VP, ctypes.POINTER(ddhf_tuning)]),
     "ddhf_bin_events": (_I32, [_VP, _VP, _VP, _VP, _VP, _I64, _I64, _I64, _VP]),
     "ddhf_export_csr": (_I32, [_VP, _VP, _VP, _I64, _VP, _VP, _VP]),
@@ -209,6 +210,20 @@ def ddhf_set_tuning(ctx, heavy_min=1024, warps_per_block=4, blocks_per_sm=0, row
 
 def ddhf_set_params(ctx, params):
     _check(load().ddhf_set_params(ctx, ctypes.byref(params)), ctx)
+
+
+def ddhf_hybrid_geometry(grid, window_us, hybrid_min):
+    """Host-only: (status, s_us, rows, threshold, dec[n_bins] numpy float32)
+    of the hybrid route for a window on this grid (no device needed)."""
+    import numpy as np
+    g = grid if isinstance(grid, ddhf_grid) else make_grid(*grid)
+    s = ctypes.c_int64()
+    rows, thr = ctypes.c_int32(), ctypes.c_int32()
+    dec = np.zeros(g.n_bins, np.float32)
+    st = load().ddhf_hybrid_geometry(ctypes.byref(g), int(window_us), int(hybrid_min),
+                                     ctypes.byref(s), ctypes.byref(rows), ctypes.byref(thr),
+                                     dec.ctypes.data_as(ctypes.c_void_p))
+    return st, s.value, rows.value, thr.value, dec
 
 
 def ddhf_set_loop_limit(ctx, limit):

@@ -97,3 +97,39 @@ def test_kernel_transform_quadratures_agree():
             np.cos(2 * np.pi * kappa * (W_PTS / 2) * np.sin(th))
         simpson = (wts * f).sum() * (th[1] - th[0]) / 3
         assert simpson == pytest.approx(es_hat(kappa), rel=1e-10, abs=1e-14)
+
+
+@pytest.mark.parametrize("grid,window_us,hybrid_min", [
+    (synth.hz_grid(0, 2, 750), 30_000, 128),
+    (synth.hz_grid(0, 1, 2000), 50_000, 32),
+    (synth.hz_grid(0, 10, 100), 20_000, 16),
+    (synth.hz_grid(97.5, 1.5, 600), 30_000, 300),
+    (synth.mode_grid(20_000, 100), 20_000, 64),
+])
+def test_library_geometry_and_deconvolution(grid, window_us, hybrid_min):
+    # the library's own plan (host code, no device) follows the stated rule,
+    # and its deconvolution factors equal 1 / psi^ by scipy's quadrature
+    from paper_2603_08386_gb300 import ddhf
+    st, s, G, thr, dec = ddhf.ddhf_hybrid_geometry(grid, window_us, hybrid_min)
+    a0, da, D, N = grid
+    assert s == D // (2 * da * N)
+    assert G == (window_us - 1) // s + W_PTS
+    assert st == 0 and thr == max(hybrid_min, 16, -(-G // 2))
+    J = N // 2
+    for j in sorted({0, 1, J - 1, J, J + 1, N - 2, N - 1, N // 3}):
+        want = 1.0 / es_hat((j - J) * da * s / D)
+        assert dec[j] == pytest.approx(want, rel=2e-7)
+    np.testing.assert_array_equal(dec[J - 1::-1][: N - 1 - J], dec[J + 1:][: J])  # even in m
+
+
+def test_library_geometry_refuses_windows_off_the_route():
+    from paper_2603_08386_gb300 import ddhf
+    g = synth.hz_grid(0, 2, 750)
+    st, s, G, thr, _ = ddhf.ddhf_hybrid_geometry(g, 400_000, 64)  # G = 1209 > 1024
+    assert (st, s, G, thr) == (5, 333, 1209, 0)
+    st, _, G, thr, _ = ddhf.ddhf_hybrid_geometry(g, 2_000, 64)    # G = 14 < 16
+    assert (st, G, thr) == (5, 14, 0)
+    st, s, _, thr, _ = ddhf.ddhf_hybrid_geometry(synth.mode_grid(20_000, 16384), 20_000, 64)
+    assert (st, s, thr) == (5, 0, 0)                               # spacing below 1 us
+    assert ddhf.ddhf_hybrid_geometry(g, 30_000, 0)[0] == 1
+    assert ddhf.ddhf_hybrid_geometry((0, 0, 10**9, 750), 30_000, 64)[0] == 1
