@@ -390,7 +390,7 @@ def test_boxes_transitive_and_fixed_point():
     rects = [(0, 0, 1, 1), (10, 0, 11, 1), (20, 0, 21, 1), (40, 0, 41, 1)]
     lab = _label_boxes(W, H, rects)
     # pairwise: dist 10 between neighbours, alpha*2 = 12 -> A-B, B-C merge; C-D: 20 > 12
-    # round 2: union box (0..21, 0..1) has max dim 22 -> alpha*22 = 132 > dist to D
+    # second merge pass: union box (0..21, 0..1) has max dim 22 -> alpha*22 = 132 > dist to D
     bx = oracle.boxes(lab, W, H, A_min=1, alpha=6.0)
     assert bx.tolist() == [[0, 0, 41, 1, 16]]
 
