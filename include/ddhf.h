@@ -146,7 +146,10 @@ typedef struct {
  *           pixel's peak (FP32 sums and hardware exp2 / rsqrt in the
  *           kernel values). A window with G < 16 or G > 1024 (or a grid with
  *           s < 1) runs BLOCKED alone. The first use allocates the path's
- *           workspace (about 64 bytes per max_events plus 12 KiB per bin). */
+ *           workspace (about 64 bytes per max_events plus 12 KiB per bin)
+ *           and copies its deconvolution factors with a synchronous copy,
+ *           so make it outside stream capture (ddhf_set_tuning with
+ *           hybrid_min > 0 does the same allocation up front). */
 #define DDHF_FORM_SINCOS 0
 #define DDHF_FORM_RECUR 1
 #define DDHF_FORM_BLOCKED 2
