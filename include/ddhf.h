@@ -376,12 +376,15 @@ ddhf_status ddhf_detect_batch_host(ddhf_ctx *ctx, const ddhf_window *windows, in
  * Backward (grad_S != NULL, S ignored): with g = grad_S,
  *   grad_f0[a] = g[a] dS_a/df0,  grad_w[h] = sum_a g[a] dS_a/dw_h,
  *   grad_sigma[h] = sum_a g[a] dS_a/dsigma_h,
+ *   grad_f[(a n_h + h - 1)(2Q+1) + q + Q] = g[a] dS_a/df_hq
+ *     = g[a] w_h G_hq P_a'(f_hq) / (Z_h B[a])   (nullable: the gradient with
+ *     respect to each evaluation frequency; dS/df0 = sum_hq h dS/df_hq),
  * using dP/df = 2 Re(conj F dF/df); sums over pixels in a fixed order. */
 ddhf_status ddhf_softcomb(ddhf_ctx *ctx, int64_t n_px, const uint32_t *pixels, const float *f0,
                           int32_t n_h, int32_t Q, double delta_hz, double tau_c_us,
                           const float *w, const float *sigma, const float *B, float *S,
                           const float *grad_S, float *grad_f0, float *grad_w, float *grad_sigma,
-                          ddhf_stream stream);
+                          float *grad_f, ddhf_stream stream);
 
 /* Median of each spectrum row P[rows][n_bins] (the mean of the two middle
  * values for an even count, as in Eq. 9-10), exact: median[rows]. */
@@ -394,22 +397,29 @@ ddhf_status ddhf_spectrum_median(ddhf_ctx *ctx, const float *P, int64_t rows, fl
  * reserved at start-up, since cudaMalloc may synchronise the device for
  * milliseconds, or a host program whose own allocator owns the device), and
  * so cannot create a context.
- * Computes the same P as ddhf_power_spectrum(DDHF_FORM_BLOCKED) with the
- * default tuning, from a per-pixel list the caller built and owns (device
- * pointers, the layout ddhf_export_csr writes): offsets[k] .. offsets[k+1]
- * index ev (packed tau | sign << 31) for pixel key k; active[n_active] lists
- * the pixel keys to evaluate; P[a * n_bins + j] for a < n_active (cap_px >=
- * n_active required). grid is a host pointer.
+ * Computes the same P, bit for bit, as ddhf_power_spectrum(DDHF_FORM_BLOCKED)
+ * with the default tuning, from a per-pixel list the caller built and owns
+ * (device pointers, the layout ddhf_export_csr writes): offsets[k] ..
+ * offsets[k+1] index ev (packed tau | sign << 31) for pixel key k, and must
+ * stay within ev[0 .. n_events) for every listed key (rows are unspecified
+ * otherwise); active[n_active] lists the pixel keys to evaluate; P[a * n_bins
+ * + j] for a < n_active (cap_px >= n_active required). grid is a host pointer.
+ * flags_dev (device uint32, nullable) receives, in stream order after the
+ * spectra, the DDHF_FLAG_* bits this call raised: DDHF_FLAG_CAPACITY when its
+ * list of heavy pixels overflowed (only possible with offsets beyond
+ * n_events; those pixels' rows are NaN).
  * Limits: n_events <= 2^25 events in ev, n_active <= 2^26. Larger sizes
  * return DDHF_ERR_INVALID_ARG. Its scratch is one fixed 256 KiB __device__
- * array (kept by every device that loads the library until exit); the first
- * call on a device looks up that array's address, so make it before any
- * stream capture. All calls share the array, so calls that overlap on the
- * GPU race: serialise them. */
+ * array (kept by every device that loads the library until exit). The first
+ * call in a CUDA context looks up that array's address and loads all of this
+ * entry point's kernels (so that later calls, on any grid, load nothing under
+ * lazy module loading): make it before any stream capture and outside any
+ * time budget. All calls share the array, so calls that overlap on the GPU
+ * race: serialise them. */
 ddhf_status ddhf_power_spectrum_noalloc(const ddhf_grid *grid, const uint32_t *offsets,
                                         const uint32_t *ev, int64_t n_events,
                                         const uint32_t *active, int64_t n_active, float *P,
-                                        int64_t cap_px, ddhf_stream stream);
+                                        int64_t cap_px, uint32_t *flags_dev, ddhf_stream stream);
 
 /* ---------------------------------------------------------------- row bands
  * The per-pixel steps (binning, Eq. 6-11) are independent per pixel, so a
@@ -529,6 +539,33 @@ ddhf_status ddhf_slide_detect(ddhf_ctx *ctx, ddhf_box *boxes, int32_t cap, int32
 
 /* Synchronise and read the sliding window's counters (host struct). */
 ddhf_status ddhf_slide_get_stats(ddhf_ctx *ctx, ddhf_slide_stats *out);
+
+/* ------------------------------------------------------ pipe peaks
+ * Not in the paper: the roofline denominators of the NDFT and comb kernels,
+ * measured on the current device instead of derived from unit counts. Four
+ * kernels each run 8 independent dependency chains per thread for `iters`
+ * steps (1 <= iters <= 2^24; 2^16 takes a few milliseconds per kernel on a
+ * GB300) on 8 blocks of 256 threads per SM, timed with CUDA events on
+ * `stream` after one warm-up launch:
+ *   ffma_per_s        FP32 fused multiply-adds per second (one per instruction),
+ *   ffma2_lane_per_s  FP32 fused multiply-adds per second issued as paired
+ *                     f32x2 instructions (two per instruction),
+ *   sin_approx_per_s  sin.approx.f32 results per second (special-function unit),
+ *   lg2_approx_per_s  lg2.approx.f32 results per second,
+ * whole device, at whatever clock the device runs during the measurement.
+ * sm_count and sm_clock_max_mhz come from the device attributes. Synchronous;
+ * allocates (and frees) one 1 KiB device buffer. out: host pointer. */
+typedef struct {
+  int32_t sm_count;
+  int32_t sm_clock_max_mhz;
+  double ffma_per_s;
+  double ffma2_lane_per_s;
+  double sin_approx_per_s;
+  double lg2_approx_per_s;
+  float elapsed_ms[4];
+} ddhf_pipe_peaks;
+
+ddhf_status ddhf_measure_pipes(ddhf_pipe_peaks *out, int32_t iters, ddhf_stream stream);
 
 /* Synchronise the context's last stream and read its counters and device
  * flags. Returns DDHF_ERR_CAPACITY / DDHF_ERR_TIMEOUT when the matching

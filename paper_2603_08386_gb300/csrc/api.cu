@@ -129,18 +129,7 @@ int ceil_log2(int64_t v) {
 
 void derive_constants(Ctx *c) {
   const ddhf_grid &g = c->grid;
-  GridConst &k = c->gconst;
-  k.a0 = (uint64_t)g.a0;
-  k.da = (uint64_t)g.da;
-  k.denom = (uint64_t)g.denom;
-  k.barrett = ~0ull / (uint64_t)g.denom;
-  k.a0_mod = (uint64_t)g.a0 % (uint64_t)g.denom;
-  k.da_mod = (uint64_t)g.da % (uint64_t)g.denom;
-  k.da16_mod = ((uint64_t)g.da * 16ull) % (uint64_t)g.denom;
-  k.da32_mod = ((uint64_t)g.da * 32ull) % (uint64_t)g.denom;
-  k.N = g.n_bins;
-  k.nbr = (g.n_bins + 31) / 32;
-  k.two_over_denom = (float)(2.0 / (double)g.denom);
+  c->gconst = make_grid_const(g);
   CombConst &cc = c->comb;
   const ddhf_params &p = c->params;
   const int N = g.n_bins;
@@ -337,11 +326,7 @@ ddhf_status ddhf_create(int32_t W, int32_t H, const ddhf_grid *grid, const ddhf_
     return DDHF_ERR_INVALID_ARG;
   if (max_events < 0 || max_events >= ((int64_t)1 << 31) || max_windows < 1 || max_windows > 4096)
     return DDHF_ERR_INVALID_ARG;
-  if (grid->a0 < 0 || grid->da <= 0 || grid->denom <= 0 || grid->denom >= ((int64_t)1 << 31) ||
-      grid->n_bins < 1 || grid->n_bins > 16384)
-    return DDHF_ERR_INVALID_ARG;
-  if ((double)grid->a0 + (double)grid->da * (grid->n_bins - 1 + 31) >= 4294967296.0)
-    return DDHF_ERR_INVALID_ARG;
+  if (!grid_ok(grid)) return DDHF_ERR_INVALID_ARG;
   ddhf_status ps = check_params(params);
   if (ps != DDHF_OK) return ps;
   ddhf_ctx *h = new (std::nothrow) ddhf_ctx();

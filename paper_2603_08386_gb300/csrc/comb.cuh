@@ -175,28 +175,7 @@ __device__ __forceinline__ void warp_sort64_regs(uint64_t &v0, uint64_t &v1) {
 
 // Mean-scaled linear bucket of a power value (monotone in the value).
 __device__ __forceinline__ int lin_bucket(float v, float scale) {
-  return (int)fminf(__fmul_rn(v, scale), 1023.f);
-}
-
-// 512 linear buckets (the fast path's histogram).
-__device__ __forceinline__ int lin_bucket512(float v, float scale) {
-  return (int)fminf(__fmul_rn(v, scale), 511.f);
-}
-
-// Smallest float v >= 0 with lin_bucket512(v, scale) >= g, for 1 <= g <= 511;
-// -1 when the search does not settle (the caller then takes an exact path).
-__device__ __forceinline__ float bucket_low(int g, float scale) {
-  float v = __fdiv_rn((float)g, scale);
-  if (!(v > 0.f) || !(v < __int_as_float(0x7f800000))) return -1.f;
-  for (int it = 0; it < 8 && v > 0.f &&
-                   lin_bucket512(__uint_as_float(__float_as_uint(v) - 1u), scale) >= g;
-       ++it)
-    v = __uint_as_float(__float_as_uint(v) - 1u);
-  for (int it = 0; it < 8 && lin_bucket512(v, scale) < g; ++it)
-    v = __uint_as_float(__float_as_uint(v) + 1u);
-  const bool ok = lin_bucket512(v, scale) >= g &&
-                  (v == 0.f || lin_bucket512(__uint_as_float(__float_as_uint(v) - 1u), scale) < g);
-  return ok ? v : -1.f;
+  return (int)fminf(fmaxf(__fmul_rn(v, scale), 0.f), 1023.f);
 }
 
 __device__ __forceinline__ float snr_of(float nw, float B) {
@@ -209,6 +188,20 @@ __device__ __forceinline__ float ln_normal(float x) {
   float r;
   asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return __fmul_rn(r, 0.693147180559945309f);
+}
+
+// Approximate reciprocal (PTX rcp.approx, flush-to-zero form).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// Base-2 logarithm of a normal float (PTX lg2.approx, flush-to-zero form).
+__device__ __forceinline__ float lg2_normal(float x) {
+  float r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
 }
 
 // N(w) = s / M_valid (Eq. 8); a power-of-two divisor is an exact scaling.
@@ -469,45 +462,74 @@ __device__ __forceinline__ CombOut comb_warp_generic(const float *Pw, const Comb
 
 
 // ------------------------------------------------------------------------
-// Fast variant for N <= 1024 bins and a median band of at most 32 ranks.
+// Fast variants for N <= 1024 bins, a median band of at most 32 ranks and at
+// most 32 bins in a candidate's harmonic windows (M (2d+1) <= 32).
 //
-// Same results as comb_warp_generic, bit for bit, with fewer instructions:
-//  * 512 linear buckets over [0, 2 mean) are filled in the same pass as the
-//    log sum of Eq. 7 (the Eq. 7 sums take 4-bin groups per lane);
-//  * the buckets holding ranks lo_r and hi_r bound the candidate set, which is
-//    extracted in one pass and sorted in registers as 32-bit keys (value bits
-//    relative to the smallest candidate, above the 10-bit bin index);
-//  * with (T, tj) the value and bin at rank lo_r, a bin lies below the band
-//    exactly when P < T, or P == T at a smaller bin index, so the bins of a
-//    window below the band are counted from the spectrum directly, with no
-//    prefix array;
-//  * one window maximum per window centre and one code byte per bin (band
-//    position, below or above the band), from which a candidate's band mask
-//    and count of bins below the band are gathered; the complement median is
-//    picked from the band values by a shuffle.
+// Same results as comb_warp_generic, bit for bit, with far fewer
+// instructions per pixel:
+//  * the log sum of Eq. 7 (base 2, scaled by ln 2 once) shares its pass with
+//    a histogram of 768 buckets linear in P over [0, 1.5 mean) (values above
+//    go to the last; two 16-bit counters per word);
+//  * the buckets holding ranks lo_r and hi_r bound the candidate bins; at
+//    most 64 candidates (about 31 on C3's spectra) are compacted into shared
+//    memory and sorted in registers as 32-bit keys (value bits relative to
+//    the smallest candidate, above the 10-bit bin index), so that lane p
+//    holds the bin of full rank lo_r + p;
+//  * one window maximum per centre (Eq. 8), then N(w) for every candidate,
+//    kept in shared memory;
+//  * candidates are evaluated one at a time by the whole warp: lane i <
+//    |H(w)| tests bin i of H(w) against the band start (bins below the band),
+//    lane p < bw tests whether the band's p-th bin lies in H(w); two ballots
+//    then locate the complement's middle ranks in the band, and SNR = N(w) /
+//    B by a correctly rounded division. The candidate with the largest N(w)
+//    goes first: its SNR bounds the best one from below, and since every
+//    complement median is at least the band start T, a candidate with
+//    N(w) / T below that bound can neither win nor tie (on C3's spectra
+//    fewer than two candidates per pixel are evaluated on average); the rest
+//    follow in increasing w.
+// Two forms share these steps. The register form (512 < N <= 768, M = 4,
+// d = 3: Table 2's comb on the 750-bin grid) gives each lane 24 consecutive
+// bins in registers, so every per-bin pass is a fixed, fully unrolled
+// sequence and the window maxima come from registers and six shuffles. The
+// shared-memory form takes any other size within the limits.
 // Pixels whose candidates do not fit (more than 64, or a value range above
 // 2^22 ulps) take an exact radix selection of the band instead.
-// Eq. 8-10 are evaluated in two phases. Every complement median lies between
-// the first and last band values T <= B <= T_hi, so LB = N_max / T_hi (the
-// largest N(w) over candidates) is a lower bound on the best SNR, and a
-// candidate with N(w) / T < LB can neither win nor tie. Phase 1 computes
-// N(w) for all candidates; phase 2 runs the exact median and division only
-// for the candidates that survive this test (or for all of them when more
-// than 64 survive).
-// Scratch layout (bytes from the scratch base, 16-byte aligned):
-//   [0, R)   R = max(5N, 2048): histogram u32[512] during selection, then the
-//            candidate values u32[64] and indices u16[64] (and the fallback's
-//            radix histogram), then the window maxima f32[N] and, from 4N,
-//            one code byte per bin: its band position 0..31, 32 below the
-//            band, 64 above it
-//   [R, R + 128)  surviving candidates u16[64]
+// Scratch (bytes from the scratch base, 16-byte aligned):
+//   [0, 1536)   histogram u32[384]; once the band's buckets are located, over
+//               it: candidate value bits u32[64] at 0 and their bins u16[64]
+//               at 256; once the band is in registers: N(w) of candidate
+//               w_lo + i, f32[n_cand] (-1: complement empty), when it fits
+//   [1536, +16 ceil(N/4))  window maxima f32[N]
+//   then N(w), when it does not fit over the histogram
 struct CombFast {
-  __host__ __device__ static int rec_bytes(int N) { return 5 * N > 2048 ? 5 * N : 2048; }
-  __host__ __device__ static int list_off(int N) { return (rec_bytes(N) + 15) & ~15; }
-  __host__ __device__ static int bytes(int N) { return list_off(N) + 128; }
+  static constexpr int kBuckets = 768;
+  static constexpr int kHist = 0;
+  static constexpr int kHistBytes = 1536;
+  static constexpr int kCandV = 0;
+  static constexpr int kCandJ = 256;
+  static constexpr int kRec = 1536;
+  __host__ __device__ static int rec_end(int N) { return kRec + ((4 * N + 15) & ~15); }
+  __host__ __device__ static int nw_off(int N, int n_cand) {
+    return 4 * n_cand <= kHistBytes ? 0 : rec_end(N);
+  }
+  __host__ __device__ static int bytes(int N, int n_cand) {
+    const int nc = n_cand > 0 ? n_cand : 0;
+    const int e = nw_off(N, nc) + 4 * nc;
+    return ((e > rec_end(N) ? e : rec_end(N)) + 15) & ~15;
+  }
   static constexpr int kMaxN = 1024;
   static constexpr int kMaxBand = 32;
-  static constexpr int kMaxList = 64;
+  static constexpr int kMaxCand = 64;
+};
+
+// The register form's shape: bins per lane, and the comb it is written for.
+struct CombReg {
+  static constexpr int kBPL = 24;
+  static constexpr int kM = 4;
+  static constexpr int kD = 3;
+  __host__ __device__ static bool fits(const CombConst &cc) {
+    return cc.N > 16 * kBPL && cc.N <= 32 * kBPL && cc.M == kM && cc.d == kD;
+  }
 };
 
 // Bitonic sort (ascending) of 32 keys, one per lane.
@@ -573,22 +595,6 @@ __device__ __forceinline__ uint64_t warp_sort32_u64(uint64_t v) {
   return v;
 }
 
-// Position of the k-th (0-based) set bit of x, or -1.
-__device__ __forceinline__ int nth_set_bit(uint32_t x, int k) {
-  int pos = 0;
-  int c = __popc(x & 0xFFFFu);
-  if (k >= c) { k -= c; x >>= 16; pos += 16; }
-  c = __popc(x & 0xFFu);
-  if (k >= c) { k -= c; x >>= 8; pos += 8; }
-  c = __popc(x & 0xFu);
-  if (k >= c) { k -= c; x >>= 4; pos += 4; }
-  c = __popc(x & 0x3u);
-  if (k >= c) { k -= c; x >>= 2; pos += 2; }
-  c = (int)(x & 1u);
-  if (k >= c) { k -= c; x >>= 1; pos += 1; }
-  return (k == 0 && (x & 1u)) ? pos : -1;
-}
-
 // The band of full ranks [lo_r, hi_r] (bw <= 32 ranks) of Pw[0..N) in the
 // (value, index) order, exactly, by radix selection of its two ends: lane p
 // gets the value bits and bin of rank lo_r + p. Returns true when the count
@@ -630,95 +636,94 @@ __device__ __forceinline__ bool below_band(float v, int j, float T, int tj) {
   return v < T || (v == T && j < tj);
 }
 
-// Window maxima and bin codes for any half-width d (the d = 3 case has an
-// inline quad version); out of line.
-__device__ __noinline__ static void comb_records_any_d(const float *Pw, int N, int d, float T,
-                                                       int tj, float *rec, uint8_t *code) {
+// Window maxima rec[c] = max of P over [c - d, c + d] for any half-width d;
+// out of line (the d = 3 case has inline versions).
+__device__ __noinline__ static void comb_records_any_d(const float *Pw, int N, int d,
+                                                       float *rec) {
   const int lane = threadIdx.x & 31;
-  for (int c = lane; c < N; c += 32) {
-    float mx = 0.f;
-    if (c >= d && c <= N - 1 - d) {
-      mx = Pw[c - d];
-      for (int i = 1; i <= 2 * d; ++i) mx = fmaxf(mx, Pw[c - d + i]);
-    }
+  for (int c = d + lane; c <= N - 1 - d; c += 32) {
+    float mx = Pw[c - d];
+    for (int i = 1; i <= 2 * d; ++i) mx = fmaxf(mx, Pw[c - d + i]);
     rec[c] = mx;
-    code[c] = below_band(Pw[c], c, T, tj) ? 32u : 64u;
   }
 }
 
-__device__ __forceinline__ CombOut comb_warp_fast(const float *Pw, const CombConst &cc,
-                                                  unsigned char *scratch) {
+// 768 linear buckets over [0, 1.5 mean) (the fast forms' histogram, with
+// scale = 512 / mean): x = v scale clamped to at most 767, bucket floor(x),
+// taken by adding 2^23 rounded down (the float bits then hold floor(x) in the
+// low mantissa bits), so no float-to-integer conversion runs on the
+// special-function pipe. Monotone in v >= 0, so the bins of a bucket range
+// are a range of full ranks, and bucket g0 <= g <= g1 exactly when g0 <= x <
+// g1 + 1. Any input (a negative value, NaN) still gives an index in [0, 1023]
+// (a histogram word index below 512: inside the scratch).
+__device__ __forceinline__ float bucket_x(float v, float scale) {
+  return fminf(__fmul_rn(v, scale), 767.f);
+}
+__device__ __forceinline__ uint32_t bucket_bits(float v, float scale) {
+  return __float_as_uint(__fadd_rd(bucket_x(v, scale), 0x1p23f));  // 0x4B000000 + g
+}
+__device__ __forceinline__ int bucket_of(float v, float scale) {
+  return (int)(bucket_bits(v, scale) & 1023u);
+}
+
+// Add one to the bucket whose bucket_bits are ybits in the packed histogram
+// (two 16-bit counters per word) at shared address hist_sa: word g >> 1, the
+// high half for odd g.
+__device__ __forceinline__ void hist_add(uint32_t hist_sa, uint32_t ybits) {
+  const uint32_t a = hist_sa + ((ybits & 1022u) << 1);
+  const uint32_t inc = (ybits & 1u) * 0xFFFFu + 1u;
+  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"(inc) : "memory");
+}
+
+// M_valid(w) = #{m <= M : m w + d <= N - 1}, the in-band harmonics (a prefix).
+__device__ __forceinline__ int comb_mvalid(int w, int M, int L) {
+  int mv = M;
+  while (mv > 0 && mv * w > L) --mv;
+  return mv;
+}
+
+// N(w) of Eq. 8 from the window maxima, or -1 when w's complement is empty
+// (KM, KD: the comb's M and d when known at compile time, else 0).
+template <int KM, int KD>
+__device__ __forceinline__ float comb_cand_nw(const float *rec, int w, const CombConst &cc,
+                                              bool uniform) {
+  const int M = KM ? KM : cc.M, d = KD ? KD : cc.d, N = cc.N;
+  const int L = N - 1 - d;
+  const int mv = uniform ? M : comb_mvalid(w, M, L);
+  const int h = w >= 2 * d + 1 ? mv * (2 * d + 1) : (mv - 1) * w + 2 * d + 1;
+  if (N - h <= 0) return -1.f;
+  float s = rec[w];  // 0 + m_1, exact
+  if (KM && uniform) {
+#pragma unroll
+    for (int m = 2; m <= KM; ++m) s = __fadd_rn(s, rec[m * w]);
+    return comb_nw(s, KM);
+  }
+#pragma unroll 4
+  for (int m = 2; m <= mv; ++m) s = __fadd_rn(s, rec[m * w]);
+  return comb_nw(s, mv);
+}
+
+// The buckets holding full ranks lo_r and hi_r in the packed histogram; lane
+// l owns buckets [24 l, 24 l + 24) (words [12 l, 12 l + 12)); the two 16-bit
+// halves never carry into each other (a bucket holds at most N <= 1024 bins,
+// 12 words at most 12288). Returns the first and last candidate bucket, the
+// bins below the first (cb) and the candidate count.
+struct BandBuckets {
+  int g0, g1, cb, ncand;
+};
+__device__ __forceinline__ BandBuckets comb_locate(const uint32_t *hist, int N, int lo_r,
+                                                   int hi_r, bool &bad) {
   const int lane = threadIdx.x & 31;
-  const int N = cc.N;
-  const uint32_t lt = lanemask_lt();
-  uint32_t *hist = reinterpret_cast<uint32_t *>(scratch);
-  uint16_t *list = reinterpret_cast<uint16_t *>(scratch + CombFast::list_off(N));
-  const float4 *P4 = reinterpret_cast<const float4 *>(Pw);
-  const int ng = (N + 3) >> 2;  // 4-bin groups, the last one possibly partial
-  CombOut out;
-  out.snr = 0.f;
-  out.w = -1;
-  out.rotor = 0;
-  out.bad = 0;
-  bool bad = false;
-
-  // ---- Eq. 7 sums (fixed order: 4-bin groups lane-strided, then a
-  // butterfly) and the histogram
-#pragma unroll
-  for (int q = 0; q < 4; ++q)
-    reinterpret_cast<uint4 *>(hist)[q * 32 + lane] = make_uint4(0u, 0u, 0u, 0u);
-  // full 4-bin groups, then the (at most 3) tail bins in the lane owning
-  // group N / 4, in bin order
-  const int nfull = N >> 2;
-  const int tail_lane = nfull & 31;
-  const int jt = nfull << 2;
-  float sum = 0.f;
-  for (int q = lane; q < nfull; q += 32) {
-    const float4 v = P4[q];
-    sum = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(sum, v.x), v.y), v.z), v.w);
-  }
-  if (lane == tail_lane)
-    for (int j = jt; j < N; ++j) sum = __fadd_rn(sum, Pw[j]);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) sum = __fadd_rn(sum, __shfl_xor_sync(0xffffffffu, sum, o));
-  const float fN = (float)N;
-  const float scale = __fdiv_rn(256.f, __fdiv_rn(sum, fN));
-  __syncwarp();
-  float slog = 0.f;
-  for (int q = lane; q < nfull; q += 32) {
-    const float4 v = P4[q];
-    slog = __fadd_rn(slog, ln_normal(fmaxf(v.x, 1e-30f)));
-    slog = __fadd_rn(slog, ln_normal(fmaxf(v.y, 1e-30f)));
-    slog = __fadd_rn(slog, ln_normal(fmaxf(v.z, 1e-30f)));
-    slog = __fadd_rn(slog, ln_normal(fmaxf(v.w, 1e-30f)));
-    atomicAdd(&hist[lin_bucket512(v.x, scale)], 1u);
-    atomicAdd(&hist[lin_bucket512(v.y, scale)], 1u);
-    atomicAdd(&hist[lin_bucket512(v.z, scale)], 1u);
-    atomicAdd(&hist[lin_bucket512(v.w, scale)], 1u);
-  }
-  if (lane == tail_lane) {
-    for (int j = jt; j < N; ++j) {
-      const float v = Pw[j];
-      slog = __fadd_rn(slog, ln_normal(fmaxf(v, 1e-30f)));
-      atomicAdd(&hist[lin_bucket512(v, scale)], 1u);
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) slog = __fadd_rn(slog, __shfl_xor_sync(0xffffffffu, slog, o));
-  out.log_sf = sum > 0.f ? __fsub_rn(__fdiv_rn(slog, fN), __logf(__fdiv_rn(sum, fN))) : 0.f;
-  if (!(out.log_sf <= cc.ln_tau_sf) || cc.w_hi < cc.w_lo) return out;
-  __syncwarp();
-
-  // ---- buckets of ranks lo_r and hi_r; lane l owns buckets [16 l, 16 l + 16)
-  const int lo_r = cc.lo_r, bw = cc.bw, hi_r = cc.lo_r + cc.bw - 1;
-  uint32_t lsum = 0;
+  uint32_t lsum;
   {
-    const uint4 *h4 = reinterpret_cast<const uint4 *>(hist) + lane * 4;
+    const uint4 *h4 = reinterpret_cast<const uint4 *>(hist) + lane * 3;  // no bank conflicts
+    uint32_t s2 = 0;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint4 t = h4[(q + (lane >> 1)) & 3];  // rotated: no bank conflicts
-      lsum += t.x + t.y + t.z + t.w;
+    for (int q = 0; q < 3; ++q) {
+      const uint4 t = h4[q];
+      s2 += t.x + t.y + t.z + t.w;
     }
+    lsum = (s2 & 0xFFFFu) + (s2 >> 16);
   }
   uint32_t tot;
   const uint32_t lex = warp_excl_scan<uint32_t>(lsum, tot);
@@ -734,7 +739,8 @@ __device__ __forceinline__ CombOut comb_warp_fast(const float *Pw, const CombCon
       bad = true;
     }
     const uint32_t base = __shfl_sync(0xffffffffu, lex, src);
-    const uint32_t h = lane < 16 ? hist[src * 16 + lane] : 0u;
+    const uint32_t wv = lane < 24 ? hist[src * 12 + (lane >> 1)] : 0u;
+    const uint32_t h = (lane & 1) ? (wv >> 16) : (wv & 0xFFFFu);
     uint32_t t2;
     const uint32_t ex = warp_excl_scan<uint32_t>(h, t2) + base;
     int s2 = __ffs(__ballot_sync(0xffffffffu, R >= ex && R < ex + h)) - 1;
@@ -742,103 +748,299 @@ __device__ __forceinline__ CombOut comb_warp_fast(const float *Pw, const CombCon
       s2 = 0;
       bad = true;
     }
-    gsel[t] = src * 16 + s2;
+    gsel[t] = src * 24 + s2;
     gbelow[t] = __shfl_sync(0xffffffffu, ex, s2);
     gcount[t] = __shfl_sync(0xffffffffu, h, s2);
   }
-  const int cb = (int)gbelow[0];  // bins in buckets below the candidates
-  const int ncand = (int)(gbelow[1] + gcount[1]) - cb;
-  bool slow = ncand > 64 || bad;
+  BandBuckets r;
+  r.g0 = gsel[0];
+  r.g1 = gsel[1];
+  r.cb = (int)gbelow[0];
+  r.ncand = (int)(gbelow[1] + gcount[1]) - r.cb;
+  return r;
+}
+
+// The band from the ncand <= 64 compacted candidates (value bits cv, bins
+// cj; element i in lane i % 32, register i / 32): sorted as 32-bit keys,
+// lane p < bw takes full rank lo_r + p (value bv, bin bj). Returns false
+// (warp-uniform) when the values span 2^22 ulps or more, so that the exact
+// selection must run instead.
+__device__ __forceinline__ bool comb_band_sorted(const unsigned char *scratch, int ncand,
+                                                 int lo_r, int cb, int bw, float &bv, int &bj,
+                                                 bool &bad) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t *cv = reinterpret_cast<const uint32_t *>(scratch + CombFast::kCandV);
+  const uint16_t *cj = reinterpret_cast<const uint16_t *>(scratch + CombFast::kCandJ);
+  const bool in0 = lane < ncand, in1 = lane + 32 < ncand;
+  const uint32_t b0 = in0 ? cv[lane] : 0xFFFFFFFFu;
+  const uint32_t b1 = in1 ? cv[lane + 32] : 0xFFFFFFFFu;
+  const uint32_t mn = __reduce_min_sync(0xffffffffu, min(b0, b1));
+  const uint32_t mx = __reduce_max_sync(0xffffffffu, max(in0 ? b0 : 0u, in1 ? b1 : 0u));
+  if (mx - mn >= (1u << 22)) return false;
+  uint32_t k0 = in0 ? (((b0 - mn) << 10) | (uint32_t)cj[lane]) : 0xFFFFFFFFu;
+  uint32_t k1 = in1 ? (((b1 - mn) << 10) | (uint32_t)cj[lane + 32]) : 0xFFFFFFFFu;
+  if (ncand <= 32) k0 = warp_sort32_u32(k0);
+  else warp_sort64_u32(k0, k1);
+  // band position p is sorted element i = lo_r - cb + p (lane i % 32, register i / 32)
+  const int i = lo_r - cb + lane;
+  const uint32_t kk0 = __shfl_sync(0xffffffffu, k0, i & 31);
+  const uint32_t kk1 = __shfl_sync(0xffffffffu, k1, i & 31);
+  const uint32_t kk = i < 32 ? kk0 : kk1;
+  if (lane < bw && (i < 0 || i >= ncand)) bad = true;
+  bv = __uint_as_float((kk >> 10) + mn);
+  bj = (int)(kk & 1023u);
+  return true;
+}
+
+// N(w) of every candidate into nws[], the largest and its candidate index
+// (the first of equal maxima; -1 / INT_MAX when every complement is empty).
+template <int KM, int KD>
+__device__ __forceinline__ void comb_nw_all(const float *rec, float *nws, const CombConst &cc,
+                                            bool uniform, float &maxnw, int &maxi) {
+  const int lane = threadIdx.x & 31;
+  const int n_cand = cc.w_hi - cc.w_lo + 1;
+  maxnw = -1.f;
+  maxi = 0x7fffffff;
+  for (int i = lane; i < n_cand; i += 32) {
+    const float nw = comb_cand_nw<KM, KD>(rec, cc.w_lo + i, cc, uniform);
+    nws[i] = nw;
+    if (nw > maxnw) {
+      maxnw = nw;
+      maxi = i;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float on = __shfl_xor_sync(0xffffffffu, maxnw, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, maxi, o);
+    if (on > maxnw || (on == maxnw && oi < maxi)) {
+      maxnw = on;
+      maxi = oi;
+    }
+  }
+}
+
+// Eq. 9-10 for the candidates, each by the whole warp: the one with the
+// largest N(w) first, then, in increasing w, those that the first one's SNR
+// does not rule out (see the description above). Lane i of a disjoint H(w)
+// (w >= 2d + 1) takes bin (1 + i / (2d+1)) w + i % (2d+1) - d; of an
+// overlapping one, bin w - d + i. Band lane p's bin lies in H(w) when it is
+// within d of m w for some m <= M_valid. bv, bj: the band value and bin of
+// lane p. KM, KD as for comb_cand_nw.
+template <int KM, int KD>
+__device__ __forceinline__ void comb_best(const float *Pw, const float *nws, const CombConst &cc,
+                                          bool uniform, float maxnw, int maxi, float bv, int bj,
+                                          float &best, int &bestw, bool &bad) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = lanemask_lt();
+  const int N = cc.N, M = KM ? KM : cc.M, d = KD ? KD : cc.d, lo_r = cc.lo_r, bw = cc.bw;
+  const int n_cand = cc.w_hi - cc.w_lo + 1;
+  const float T = __shfl_sync(0xffffffffu, bv, 0);  // band start (T, tj)
+  const int tj = __shfl_sync(0xffffffffu, bj, 0);
+  const int span = 2 * d + 1;
+  const int lane_m = 1 + lane / span, lane_o = lane % span - d;
+  const bool band_lane = lane < bw;
+  // SNR of candidate w with N(w) = nw
+  auto eval = [&](int w, float nw) -> float {
+    const int mv = uniform ? M : comb_mvalid(w, M, N - 1 - d);
+    const bool disjoint = w >= span;
+    const int h = disjoint ? mv * span : (mv - 1) * w + span;
+    const int c = N - h;
+    // bins of H(w) below the band
+    const int j = disjoint ? lane_m * w + lane_o : w - d + lane;
+    const bool blw = lane < h && below_band(Pw[lane < h ? j : 0], j, T, tj);
+    const int below = __popc(__ballot_sync(0xffffffffu, blw));
+    // band positions inside H(w)
+    bool rm = false;
+    if (KM && uniform) {
+#pragma unroll
+      for (int m = 1; m <= KM; ++m) rm |= (uint32_t)(bj - m * w + d) <= (uint32_t)(2 * d);
+    } else {
+      for (int m = 1; m <= mv; ++m) rm |= (uint32_t)(bj - m * w + d) <= (uint32_t)(2 * d);
+    }
+    const bool fr = band_lane && !rm;
+    const uint32_t fb = __ballot_sync(0xffffffffu, fr);
+    const int rank = __popc(fb & lt);
+    const int t = (c - 1) / 2 - (lo_r - below);
+    int pos0 = __ffs(__ballot_sync(0xffffffffu, fr && rank == t)) - 1;
+    int pos1 = (c & 1) ? pos0 : __ffs(__ballot_sync(0xffffffffu, fr && rank == t + 1)) - 1;
+    if (pos0 < 0 || pos1 < 0) {
+      pos0 = pos1 = 0;
+      bad = true;
+    }
+    const float v0 = __shfl_sync(0xffffffffu, bv, pos0);
+    const float v1 = __shfl_sync(0xffffffffu, bv, pos1);
+    const float B = (c & 1) ? v0 : __fmul_rn(__fadd_rn(v0, v1), 0.5f);
+    return snr_of(nw, B);
+  };
+  best = 0.f;
+  bestw = -1;
+  const int wstar = maxnw >= 0.f ? cc.w_lo + maxi : -1;
+  float thr = 0.f;
+  if (wstar >= 0) {
+    best = eval(wstar, maxnw);
+    bestw = wstar;
+    // keep w when N(w) >= thr: thr <= best T (1 - 2^-20) (1 + 2^-23), so a
+    // dropped candidate has N(w) / T < best (1 - 2^-21) and SNR(w) < best
+    // (best and best T normal and finite, so that the rounding bounds hold)
+    const float bt = __fmul_rn(best, T);
+    const bool prune = T > 0.f && best >= 0x1p-126f && best < __int_as_float(0x7f800000) &&
+                       bt >= 0x1p-100f && bt < __int_as_float(0x7f800000);
+    thr = prune ? __fmul_rn(bt, 1.0f - 0x1p-20f) : 0.f;
+  }
+  for (int i0 = 0; i0 < n_cand; i0 += 32) {
+    const int i = i0 + lane;
+    const float nwl = i < n_cand ? nws[i] : -1.f;
+    uint32_t sm = __ballot_sync(0xffffffffu, nwl >= 0.f && nwl >= thr && cc.w_lo + i != wstar);
+    while (sm) {
+      const int src = __ffs(sm) - 1;
+      sm &= sm - 1;
+      const int w = cc.w_lo + i0 + src;
+      const float snr = eval(w, __shfl_sync(0xffffffffu, nwl, src));
+      if (snr > best || (snr == best && w < bestw)) {
+        best = snr;
+        bestw = w;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ CombOut comb_out(float best, int bestw, bool bad, float log_sf,
+                                            const CombConst &cc) {
+  CombOut out;
+  out.log_sf = log_sf;
+  out.bad = __any_sync(0xffffffffu, bad) ? 1 : 0;
+  out.snr = bestw >= 0 ? best : 0.f;
+  out.w = bestw;
+  out.rotor = (bestw >= 0 && best >= cc.tau_comb) ? 1 : 0;
+  return out;
+}
+
+// The shared-memory form (any size within the fast limits).
+__device__ __forceinline__ CombOut comb_warp_fast_smem(const float *Pw, const CombConst &cc,
+                                                       unsigned char *scratch) {
+  const int lane = threadIdx.x & 31;
+  const int N = cc.N;
+  uint32_t *hist = reinterpret_cast<uint32_t *>(scratch + CombFast::kHist);
+  const uint32_t hist_sa = (uint32_t)__cvta_generic_to_shared(hist);
+  const float4 *P4 = reinterpret_cast<const float4 *>(Pw);
+  const int ng = (N + 3) >> 2;  // 4-bin groups, the last one possibly partial
+  CombOut out;
+  out.snr = 0.f;
+  out.w = -1;
+  out.rotor = 0;
+  out.bad = 0;
+  bool bad = false;
+
+  // ---- Eq. 7 sums (fixed order: 4-bin groups lane-strided, the (at most 3)
+  // tail bins in the lane owning group N / 4, then a butterfly) and the
+  // histogram
+#pragma unroll
+  for (int q = 0; q < CombFast::kHistBytes / 512; ++q)
+    reinterpret_cast<uint4 *>(hist)[q * 32 + lane] = make_uint4(0u, 0u, 0u, 0u);
+  const int nfull = N >> 2;
+  const int tail_lane = nfull & 31;
+  const int jt = nfull << 2;
+  float sum = 0.f;
+  for (int q = lane; q < nfull; q += 32) {
+    const float4 v = P4[q];
+    sum = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(sum, v.x), v.y), v.z), v.w);
+  }
+  if (lane == tail_lane)
+    for (int j = jt; j < N; ++j) sum = __fadd_rn(sum, Pw[j]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sum = __fadd_rn(sum, __shfl_xor_sync(0xffffffffu, sum, o));
+  const float fN = (float)N;
+  const float scale = __fdiv_rn(512.f, __fdiv_rn(sum, fN));
+  __syncwarp();
+  float sl2 = 0.f;  // sum of log2 max(P, 1e-30)
+  for (int q = lane; q < nfull; q += 32) {
+    const float4 v = P4[q];
+    sl2 = __fadd_rn(sl2, lg2_normal(fmaxf(v.x, 1e-30f)));
+    sl2 = __fadd_rn(sl2, lg2_normal(fmaxf(v.y, 1e-30f)));
+    sl2 = __fadd_rn(sl2, lg2_normal(fmaxf(v.z, 1e-30f)));
+    sl2 = __fadd_rn(sl2, lg2_normal(fmaxf(v.w, 1e-30f)));
+    hist_add(hist_sa, bucket_bits(v.x, scale));
+    hist_add(hist_sa, bucket_bits(v.y, scale));
+    hist_add(hist_sa, bucket_bits(v.z, scale));
+    hist_add(hist_sa, bucket_bits(v.w, scale));
+  }
+  if (lane == tail_lane) {
+    for (int j = jt; j < N; ++j) {
+      const float v = Pw[j];
+      sl2 = __fadd_rn(sl2, lg2_normal(fmaxf(v, 1e-30f)));
+      hist_add(hist_sa, bucket_bits(v, scale));
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sl2 = __fadd_rn(sl2, __shfl_xor_sync(0xffffffffu, sl2, o));
+  const float slog = __fmul_rn(sl2, 0.693147180559945309f);
+  out.log_sf = sum > 0.f ? __fsub_rn(__fdiv_rn(slog, fN), __logf(__fdiv_rn(sum, fN))) : 0.f;
+  if (!(out.log_sf <= cc.ln_tau_sf) || cc.w_hi < cc.w_lo) return out;
   __syncwarp();
 
   // ---- the band: lane p < bw holds the bin at full rank lo_r + p
+  const int lo_r = cc.lo_r, bw = cc.bw, hi_r = cc.lo_r + cc.bw - 1;
+  const BandBuckets bb = comb_locate(hist, N, lo_r, hi_r, bad);
+  bool slow = bb.ncand > CombFast::kMaxCand || bad;
   float bv = 0.f;  // its value
   int bj = 0;      // its bin
-  float T = 0.f;   // band start in the (value, index) order: (T, tj)
-  int tj = 0;
   if (!slow) {
-    uint32_t *cv = hist;                                         // u32[64]
-    uint16_t *cj = reinterpret_cast<uint16_t *>(scratch + 256);  // u16[64]
-    // candidates are the bins with vlo <= P < vhi, the value bounds of buckets
-    // gsel[0] .. gsel[1] (exact: checked against the bucket function)
-    const float vlo = gsel[0] == 0 ? 0.f : bucket_low(gsel[0], scale);
-    const float vhi = gsel[1] >= 511 ? __int_as_float(0x7f800000) : bucket_low(gsel[1] + 1, scale);
-    if (vlo < 0.f || vhi < 0.f) slow = true;
-    uint32_t run = 0;
-    for (int q0 = 0; q0 < ng; q0 += 32) {
-      const int q = q0 + lane;
-      const float4 v = q < ng ? P4[q] : make_float4(-1.f, -1.f, -1.f, -1.f);
-      const float e[4] = {v.x, v.y, v.z, v.w};
+    // this lane's candidates: bit 4k + u for element u of group lane + 32 k
+    const uint32_t g0 = (uint32_t)bb.g0, gspan = (uint32_t)(bb.g1 - bb.g0);
+    uint32_t m = 0;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int j = 4 * q + u;
-        const bool in = e[u] >= vlo && e[u] < vhi && j < N;
-        const uint32_t bi = __ballot_sync(0xffffffffu, in);
-        if (in) {
-          const uint32_t slot = run + __popc(bi & lt);
-          if (slot < 64) {
-            cv[slot] = __float_as_uint(e[u]);
-            cj[slot] = (uint16_t)j;
-          }
-        }
-        run += __popc(bi);
+    for (int k = 0; k < 8; ++k) {
+      const int q = lane + 32 * k;
+      if (32 * k < ng && q < ng) {
+        const float4 v = P4[q];
+        const int j = 4 * q;
+        m |= ((uint32_t)(bucket_of(v.x, scale) - g0) <= gspan ? 1u : 0u) << (4 * k);
+        m |= ((uint32_t)(bucket_of(v.y, scale) - g0) <= gspan && j + 1 < N ? 1u : 0u)
+             << (4 * k + 1);
+        m |= ((uint32_t)(bucket_of(v.z, scale) - g0) <= gspan && j + 2 < N ? 1u : 0u)
+             << (4 * k + 2);
+        m |= ((uint32_t)(bucket_of(v.w, scale) - g0) <= gspan && j + 3 < N ? 1u : 0u)
+             << (4 * k + 3);
       }
     }
-    if ((int)run != ncand) slow = true;
-    __syncwarp();
-    const bool in0 = lane < ncand, in1 = lane + 32 < ncand;
-    const uint32_t b0 = in0 ? cv[lane] : 0xFFFFFFFFu;
-    const uint32_t b1 = in1 ? cv[lane + 32] : 0xFFFFFFFFu;
-    const uint32_t j0v = in0 ? cj[lane] : 0u;
-    const uint32_t j1v = in1 ? cj[lane + 32] : 0u;
-    const uint32_t mn = __reduce_min_sync(0xffffffffu, min(b0, b1));
-    const uint32_t mx = __reduce_max_sync(0xffffffffu, max(in0 ? b0 : 0u, in1 ? b1 : 0u));
-    if (slow || mx - mn >= (1u << 22)) {
-      slow = true;
-    } else {
-      uint32_t k0 = in0 ? (((b0 - mn) << 10) | j0v) : 0xFFFFFFFFu;
-      uint32_t k1 = in1 ? (((b1 - mn) << 10) | j1v) : 0xFFFFFFFFu;
-      if (ncand <= 32) {
-        k0 = warp_sort32_u32(k0);
-      } else {
-        warp_sort64_u32(k0, k1);
+    uint32_t nsel;
+    uint32_t off = warp_excl_scan<uint32_t>((uint32_t)__popc(m), nsel);
+    if ((int)nsel != bb.ncand) slow = true;  // uniform (a reduction)
+    if (!slow) {
+      uint32_t *cv = reinterpret_cast<uint32_t *>(scratch + CombFast::kCandV);
+      uint16_t *cj = reinterpret_cast<uint16_t *>(scratch + CombFast::kCandJ);
+      while (m) {
+        const int b = __ffs(m) - 1;
+        m &= m - 1;
+        const int j = 4 * (lane + 32 * (b >> 2)) + (b & 3);
+        cv[off] = __float_as_uint(Pw[j]);
+        cj[off] = (uint16_t)j;
+        ++off;
       }
-      // sorted element i sits in lane i % 32, register i / 32; band position
-      // p is sorted element p0 + p
-      const int p0 = lo_r - cb;
-      const int i = p0 + lane;
-      const int src = i & 31;
-      const uint32_t kk0 = __shfl_sync(0xffffffffu, k0, src);
-      const uint32_t kk1 = __shfl_sync(0xffffffffu, k1, src);
-      const uint32_t key = i < 32 ? kk0 : kk1;
-      if (lane < bw && i >= ncand) bad = true;
-      bv = __uint_as_float((key >> 10) + mn);
-      bj = (int)(key & 1023u);
-      T = __shfl_sync(0xffffffffu, bv, 0);
-      tj = __shfl_sync(0xffffffffu, bj, 0);
+      __syncwarp();
+      if (!comb_band_sorted(scratch, bb.ncand, lo_r, bb.cb, bw, bv, bj, bad)) slow = true;
+      __syncwarp();
     }
-    __syncwarp();
   }
   if (slow) {
     // exact band [lo_r, hi_r] by radix selection (a rare, out-of-line path)
     uint32_t bvu = 0u;
+    __syncwarp();
     bad |= comb_band_exact(Pw, N, lo_r, hi_r, bw, hist, bvu, bj);
     bv = __uint_as_float(bvu);
-    T = __shfl_sync(0xffffffffu, bv, 0);
-    tj = __shfl_sync(0xffffffffu, bj, 0);
     __syncwarp();
   }
 
-  // ---- window maxima: rec[c] = max of P over [c - d, c + d]; bin codes
+  // ---- window maxima: rec[c] = max of P over [c - d, c + d] (centres
+  // d .. N-1-d are the ones read)
   const int d = cc.d;
-  float *rec = reinterpret_cast<float *>(scratch);
-  uint8_t *code = scratch + 4 * N;
+  float *rec = reinterpret_cast<float *>(scratch + CombFast::kRec);
   if (d == 3) {
     // centre quads 4q .. 4q + 3: bins 4q - 4 .. 4q + 7 by three 16-byte loads
-    const int nq4 = N >> 2;  // quads whose bins 4q .. 4q + 3 are all < N
     for (int q = lane; q < ng; q += 32) {
       float b[12];  // b[i] = P[4q - 4 + i]
-      if (q >= 1 && q + 1 < nq4) {
+      if (q >= 1 && q + 1 < nfull) {
         const float4 x = P4[q - 1], y = P4[q], z = P4[q + 1];
         b[0] = x.x; b[1] = x.y; b[2] = x.z; b[3] = x.w;
         b[4] = y.x; b[5] = y.y; b[6] = y.z; b[7] = y.w;
@@ -857,275 +1059,242 @@ __device__ __forceinline__ CombOut comb_warp_fast(const float *Pw, const CombCon
       const float w2 = fmaxf(mid, fmaxf(b[3], r1));   // 4q-1 .. 4q+5
       const float w3 = fmaxf(mid, fmaxf(r1, b[10]));  // 4q   .. 4q+6
       const int j0 = 4 * q;
-      const uint32_t k0 = below_band(b[4], j0, T, tj) ? 32u : 64u;
-      const uint32_t k1 = below_band(b[5], j0 + 1, T, tj) ? 32u : 64u;
-      const uint32_t k2 = below_band(b[6], j0 + 2, T, tj) ? 32u : 64u;
-      const uint32_t k3 = below_band(b[7], j0 + 3, T, tj) ? 32u : 64u;
-      if (q < nq4) {
+      if (q < nfull) {
         reinterpret_cast<float4 *>(rec)[q] = make_float4(w0, w1, w2, w3);
-        reinterpret_cast<uint32_t *>(code)[q] = k0 | (k1 << 8) | (k2 << 16) | (k3 << 24);
       } else {  // the partial last quad
         const float wv[4] = {w0, w1, w2, w3};
-        const uint32_t kv[4] = {k0, k1, k2, k3};
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          if (j0 + u < N) {
-            rec[j0 + u] = wv[u];
-            code[j0 + u] = (uint8_t)kv[u];
-          }
+          if (j0 + u < N) rec[j0 + u] = wv[u];
       }
     }
   } else {
-    comb_records_any_d(Pw, N, d, T, tj, rec, code);
+    comb_records_any_d(Pw, N, d, rec);
   }
   __syncwarp();
-  if (lane < bw) code[bj] = (uint8_t)lane;
+
+  // ---- Eq. 8-10. When every candidate has M_valid = M and a non-empty
+  // complement (always for h_min >= M and N > M(2d+1)), N(w) is a plain sum
+  // over M windows.
+  const bool uniform = cc.M * cc.w_hi <= N - 1 - d && N > cc.M * (2 * d + 1);
+  float *nws = reinterpret_cast<float *>(scratch + CombFast::nw_off(N, cc.w_hi - cc.w_lo + 1));
+  float maxnw;
+  int maxi;
+  comb_nw_all<0, 0>(rec, nws, cc, uniform, maxnw, maxi);
   __syncwarp();
-
-  // ---- Eq. 8-10, phase 1: N(w) of every candidate and the largest one.
-  // When every candidate has M_valid = M and a non-empty complement (always
-  // for h_min >= M and N > M(2d+1)), N(w) is a plain sum over M windows.
-  const int L = N - 1 - d;
-  const int M = cc.M;
-  const int n_cand = cc.w_hi - cc.w_lo + 1;
-  const bool uniform = M * cc.w_hi <= L && N > M * (2 * d + 1);
-  // In the uniform case with at most 256 candidates, lane l keeps the window
-  // sums of its candidates l + 32 k in registers for the survivor pass.
-  constexpr int kSlots = 8;
-  const bool in_regs = uniform && n_cand <= 32 * kSlots;
-  float sv[kSlots];
-  float maxnw = 0.f;
-  if (in_regs) {
-    float maxs = 0.f;
-#pragma unroll
-    for (int k = 0; k < kSlots; ++k) {
-      sv[k] = 0.f;
-      if (32 * k < n_cand) {
-        const int i = 32 * k + lane;
-        const int w = cc.w_lo + i;
-        if (i < n_cand) {
-          float s = 0.f;
-          int c0 = 0;
-#pragma unroll 4
-          for (int m = 0; m < M; ++m) {
-            c0 += w;
-            s = __fadd_rn(s, rec[c0]);
-          }
-          sv[k] = s;
-          maxs = fmaxf(maxs, s);  // same order as N(w): a common scaling
-        }
-      }
-    }
-    maxnw = comb_nw(maxs, M);
-  } else if (uniform) {
-    for (int i0 = 0; i0 < n_cand; i0 += 32) {
-      const int w = cc.w_lo + i0 + lane;
-      if (i0 + lane < n_cand) {
-        float s = 0.f;
-        int c0 = 0;
-#pragma unroll 4
-        for (int m = 0; m < M; ++m) {
-          c0 += w;
-          s = __fadd_rn(s, rec[c0]);
-        }
-        maxnw = fmaxf(maxnw, s);
-      }
-    }
-    maxnw = comb_nw(maxnw, M);
-  } else {
-    for (int i0 = 0; i0 < n_cand; i0 += 32) {
-      const int w = cc.w_lo + i0 + lane;
-      if (i0 + lane < n_cand) {
-        int mv = M;
-        while (mv * w > L) --mv;
-        const int h = w >= 2 * d + 1 ? mv * (2 * d + 1) : (mv - 1) * w + 2 * d + 1;
-        float s = 0.f;
-        int c0 = 0;
-        for (int m = 1; m <= mv; ++m) {
-          c0 += w;
-          s = __fadd_rn(s, rec[c0]);
-        }
-        if (N - h > 0) maxnw = fmaxf(maxnw, comb_nw(s, mv));
-      }
-    }
-  }
-  maxnw = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(maxnw)));  // >= 0
-  const float Thi = __shfl_sync(0xffffffffu, bv, bw - 1);
-  const float LB = snr_of(maxnw, Thi);
-  // keep w when N(w) >= thr; thr <= LB T (1 - 2^-20) (1 + 2^-23), so a
-  // dropped candidate has N(w) / T < LB (1 - 2^-21) and SNR(w) < LB
-  // (LB and LB T normal and finite, so that the relative rounding bounds hold)
-  const float lbt = __fmul_rn(LB, T);
-  const bool prune = T > 0.f && LB >= 0x1p-126f && LB < __int_as_float(0x7f800000) &&
-                     lbt >= 0x1p-100f && lbt < __int_as_float(0x7f800000);
-  const float thr = prune ? __fmul_rn(lbt, 1.0f - 0x1p-20f) : 0.f;
-
-  // ---- surviving candidates, in increasing w
-  int n_items = n_cand;
-  bool use_list = false;
-  if (prune) {
-    uint32_t run = 0;
-    if (in_regs) {
-#pragma unroll
-      for (int k = 0; k < kSlots; ++k) {
-        if (32 * k < n_cand) {
-          const int i = 32 * k + lane;
-          const bool keep = i < n_cand && comb_nw(sv[k], M) >= thr;
-          const uint32_t b = __ballot_sync(0xffffffffu, keep);
-          const uint32_t slot = run + __popc(b & lt);
-          if (keep && slot < (uint32_t)CombFast::kMaxList) list[slot] = (uint16_t)(cc.w_lo + i);
-          run += __popc(b);
-        }
-      }
-    } else {
-      for (int i0 = 0; i0 < n_cand; i0 += 32) {
-        const int w = cc.w_lo + i0 + lane;
-        bool keep = false;
-        if (i0 + lane < n_cand) {
-          int mv = M;
-          if (!uniform)
-            while (mv * w > L) --mv;
-          float s = 0.f;
-          int c0 = 0;
-#pragma unroll 4
-          for (int m = 1; m <= mv; ++m) {
-            c0 += w;
-            s = __fadd_rn(s, rec[c0]);
-          }
-          keep = comb_nw(s, mv) >= thr;
-        }
-        const uint32_t b = __ballot_sync(0xffffffffu, keep);
-        const uint32_t slot = run + __popc(b & lt);
-        if (keep && slot < (uint32_t)CombFast::kMaxList) list[slot] = (uint16_t)w;
-        run += __popc(b);
-      }
-    }
-    if (run <= (uint32_t)CombFast::kMaxList) {
-      use_list = true;
-      n_items = (int)run;
-    }
-    __syncwarp();
-  }
-
-  // ---- phase 2: exact SNR of the surviving candidates, 32 at a time, one
-  // per lane. The band mask of H(w) and its bins below the band are gathered
-  // from the bin codes by a group of g lanes per candidate (g the largest
-  // power of two with nk g <= 32; each lane takes every g-th bin of H(w)) and
-  // combined within the group, then handed to the candidate's lane.
-  const uint32_t outside = bw >= 32 ? 0u : (0xFFFFFFFFu << bw);
-  float best = 0.f;
-  int bestw = -1;
-  for (int i0 = 0; i0 < n_items; i0 += 32) {
-    const int nk = min(32, n_items - i0);
-    const int wl = lane < nk ? (use_list ? (int)list[i0 + lane] : cc.w_lo + i0 + lane) : 1;
-    const int g = nk > 16 ? 1 : nk > 8 ? 2 : nk > 4 ? 4 : nk > 2 ? 8 : nk > 1 ? 16 : 32;
-    const int gk = lane / g, gs = lane - gk * g;
-    const int wk = __shfl_sync(0xffffffffu, wl, gk < nk ? gk : 0);
-    uint32_t gmask = 0u;
-    int gbelow = 0;
-    if (gk < nk) {
-      int mvk = M;
-      while (mvk * wk > L) --mvk;
-      if (wk >= 2 * d + 1) {
-        for (int m = 1; m <= mvk; ++m) {
-          for (int i = gs - d; i <= d; i += g) {
-            const uint32_t k = code[m * wk + i];
-            gmask |= __funnelshift_lc(0u, 1u, k);  // 1 << k, 0 for k >= 32
-            gbelow += (int)((k >> 5) & 1u);
-          }
-        }
-      } else {  // overlapping windows: one range
-        for (int j = wk - d + gs; j <= mvk * wk + d; j += g) {
-          const uint32_t k = code[j];
-          gmask |= __funnelshift_lc(0u, 1u, k);
-          gbelow += (int)((k >> 5) & 1u);
-        }
-      }
-    }
-    for (int o = g >> 1; o > 0; o >>= 1) {
-      gmask |= __shfl_xor_sync(0xffffffffu, gmask, o);
-      gbelow += __shfl_xor_sync(0xffffffffu, gbelow, o);
-    }
-    const int lead = lane * g < 32 ? lane * g : 0;
-    const uint32_t my_mask = __shfl_sync(0xffffffffu, gmask, lead);
-    const int my_below = __shfl_sync(0xffffffffu, gbelow, lead);
-    const bool ok = lane < nk;
-    const int w = wl;
-    int pos0 = 0, pos1 = 0, c = 0, mv = 1;
-    float s = 0.f;
-    if (ok) {
-      mv = M;
-      while (mv * w > L) --mv;
-      int c0 = 0;
-#pragma unroll 4
-      for (int m = 1; m <= mv; ++m) {
-        c0 += w;
-        s = __fadd_rn(s, rec[c0]);
-      }
-      const int h = w >= 2 * d + 1 ? mv * (2 * d + 1) : (mv - 1) * w + 2 * d + 1;
-      c = N - h;
-      if (c > 0) {
-        const int t = (c - 1) / 2 - (lo_r - my_below);
-        const uint32_t freeb = ~(my_mask | outside);
-        pos0 = t >= 0 ? nth_set_bit(freeb, t) : -1;
-        if (pos0 < 0) {
-          pos0 = 0;
-          bad = true;
-        }
-        const uint32_t rest = pos0 >= 31 ? 0u : (freeb & (0xFFFFFFFEu << pos0));
-        pos1 = (c & 1) ? pos0 : __ffs(rest) - 1;
-        if (pos1 < 0) {
-          pos1 = 0;
-          bad = true;
-        }
-      }
-    }
-    const float v0 = __shfl_sync(0xffffffffu, bv, pos0);
-    const float v1 = __shfl_sync(0xffffffffu, bv, pos1);
-    if (ok && c > 0) {
-      const float B = (c & 1) ? v0 : __fmul_rn(__fadd_rn(v0, v1), 0.5f);
-      const float snr = snr_of(comb_nw(s, mv), B);
-      if (bestw < 0 || snr > best || (snr == best && w < bestw)) {
-        best = snr;
-        bestw = w;
-      }
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-    const int ow = __shfl_xor_sync(0xffffffffu, bestw, o);
-    if (ow >= 0 && (bestw < 0 || ob > best || (ob == best && ow < bestw))) {
-      best = ob;
-      bestw = ow;
-    }
-  }
-  out.bad = __any_sync(0xffffffffu, bad) ? 1 : 0;
-  out.snr = bestw >= 0 ? best : 0.f;
-  out.w = bestw;
-  out.rotor = (bestw >= 0 && best >= cc.tau_comb) ? 1 : 0;
+  float best;
+  int bestw;
+  comb_best<0, 0>(Pw, nws, cc, uniform, maxnw, maxi, bv, bj, best, bestw, bad);
+  out = comb_out(best, bestw, bad, out.log_sf, cc);
   __syncwarp();
   return out;
 }
 
-// Which comb variant a context uses: 0 = fast (N <= 1024, band <= 32),
-// otherwise the generic one with NW mask words per centre.
+// The register form: 512 < N <= 768 bins, M = 4, d = 3. Lane l holds bins
+// [24 l, 24 l + 24) in v[0..5] (bins at or beyond N as zeros); the lane's own
+// sums run in bin order, then a butterfly. The zeros of the last lanes add
+// nothing to the sum, lg2(1e-30) each to the log sum and one each to bucket 0
+// of the histogram; both are taken back out, so the results are those of the
+// N bins.
+__device__ __forceinline__ CombOut comb_warp_fast_regs(const float *Pw, const CombConst &cc,
+                                                       unsigned char *scratch) {
+  constexpr int kB = CombReg::kBPL, kM = CombReg::kM, kD = CombReg::kD;
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = lanemask_lt();
+  const int N = cc.N;
+  uint32_t *hist = reinterpret_cast<uint32_t *>(scratch + CombFast::kHist);
+  const uint32_t hist_sa = (uint32_t)__cvta_generic_to_shared(hist);
+  CombOut out;
+  out.snr = 0.f;
+  out.w = -1;
+  out.rotor = 0;
+  out.bad = 0;
+  bool bad = false;
+#pragma unroll
+  for (int q = 0; q < CombFast::kHistBytes / 512; ++q)
+    reinterpret_cast<uint4 *>(hist)[q * 32 + lane] = make_uint4(0u, 0u, 0u, 0u);
+  // ---- the lane's 24 bins
+  const int base = kB * lane;
+  const int nval = min(max(N - base, 0), kB);  // bins of this lane below N
+  float v[kB];
+  {
+    const float4 *P4 = reinterpret_cast<const float4 *>(Pw) + base / 4;
+#pragma unroll
+    for (int k = 0; k < kB / 4; ++k) {
+      float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (4 * k < nval) {
+        t = P4[k];
+        const int r = nval - 4 * k;  // the group may run past N: those bins become zeros
+        if (r < 4) {
+          if (r < 2) t.y = 0.f;
+          if (r < 3) t.z = 0.f;
+          t.w = 0.f;
+        }
+      }
+      v[4 * k] = t.x;
+      v[4 * k + 1] = t.y;
+      v[4 * k + 2] = t.z;
+      v[4 * k + 3] = t.w;
+    }
+  }
+  // ---- Eq. 7 sums and the histogram
+  float sum = 0.f;
+#pragma unroll
+  for (int i = 0; i < kB; ++i) sum = __fadd_rn(sum, v[i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sum = __fadd_rn(sum, __shfl_xor_sync(0xffffffffu, sum, o));
+  const float fN = (float)N;
+  const float scale = __fdiv_rn(512.f, __fdiv_rn(sum, fN));
+  __syncwarp();
+  float sl2 = 0.f;
+#pragma unroll
+  for (int i = 0; i < kB; ++i) {
+    sl2 = __fadd_rn(sl2, lg2_normal(fmaxf(v[i], 1e-30f)));
+    hist_add(hist_sa, bucket_bits(v[i], scale));
+  }
+  const int npad = kB - nval;
+  if (npad > 0) {
+    sl2 = __fmaf_rn(-(float)npad, lg2_normal(1e-30f), sl2);
+    atomicSub(&hist[0], (uint32_t)npad);  // bucket 0 is the low half of word 0
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sl2 = __fadd_rn(sl2, __shfl_xor_sync(0xffffffffu, sl2, o));
+  const float slog = __fmul_rn(sl2, 0.693147180559945309f);
+  out.log_sf = sum > 0.f ? __fsub_rn(__fdiv_rn(slog, fN), __logf(__fdiv_rn(sum, fN))) : 0.f;
+  if (!(out.log_sf <= cc.ln_tau_sf) || cc.w_hi < cc.w_lo) return out;
+  __syncwarp();
+
+  // ---- window maxima of the lane's centres from its bins and three bins of
+  // each neighbour: b[i] = P[base - 3 + i], i = 0..29; centres 4k .. 4k+3 of
+  // the lane need b[4k .. 4k+9]
+  float *rec = reinterpret_cast<float *>(scratch + CombFast::kRec);
+  {
+    float lft[kD], rgt[kD];
+#pragma unroll
+    for (int i = 0; i < kD; ++i) {
+      lft[i] = __shfl_up_sync(0xffffffffu, v[kB - kD + i], 1);
+      rgt[i] = __shfl_down_sync(0xffffffffu, v[i], 1);
+    }
+    float4 *r4 = reinterpret_cast<float4 *>(rec) + base / 4;
+#pragma unroll
+    for (int k = 0; k < kB / 4; ++k) {
+      float b[10];
+#pragma unroll
+      for (int i = 0; i < 10; ++i) {
+        const int src = 4 * k + i - kD;  // bin of the lane, -3 .. 26
+        b[i] = src < 0 ? lft[src + kD] : (src >= kB ? rgt[src - kB] : v[src]);
+      }
+      const float mid = fmaxf(fmaxf(b[3], b[4]), fmaxf(b[5], b[6]));
+      const float l1 = fmaxf(b[1], b[2]), r1 = fmaxf(b[7], b[8]);
+      const float w0 = fmaxf(mid, fmaxf(b[0], l1));
+      const float w1 = fmaxf(mid, fmaxf(l1, b[7]));
+      const float w2 = fmaxf(mid, fmaxf(b[2], r1));
+      const float w3 = fmaxf(mid, fmaxf(r1, b[9]));
+      if (4 * k < nval) r4[k] = make_float4(w0, w1, w2, w3);
+    }
+  }
+
+  // ---- the band: lane p < bw holds the bin at full rank lo_r + p
+  const int lo_r = cc.lo_r, bw = cc.bw, hi_r = cc.lo_r + cc.bw - 1;
+  const BandBuckets bb = comb_locate(hist, N, lo_r, hi_r, bad);
+  bool slow = bb.ncand > CombFast::kMaxCand || bad;
+  float bv = 0.f;
+  int bj = 0;
+  if (!slow) {
+    // the lane's candidates as a bit mask over its 24 bins (read back from
+    // shared memory, so that its registers are free for the selection), then
+    // compacted in bin order
+    uint32_t *cv = reinterpret_cast<uint32_t *>(scratch + CombFast::kCandV);
+    uint16_t *cj = reinterpret_cast<uint16_t *>(scratch + CombFast::kCandJ);
+    const float x0 = (float)bb.g0, x1 = (float)(bb.g1 + 1);
+    const float4 *P4 = reinterpret_cast<const float4 *>(Pw) + base / 4;
+    uint32_t m = 0;
+#pragma unroll
+    for (int k = 0; k < kB / 4; ++k) {
+      const float4 t = 4 * k < nval ? P4[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float e[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float x = bucket_x(e[u], scale);
+        m |= (x >= x0 && x < x1 ? 1u : 0u) << (4 * k + u);
+      }
+    }
+    m &= nval >= kB ? 0xFFFFFFu : (nval > 0 ? (1u << nval) - 1u : 0u);
+    uint32_t run;
+    uint32_t off = warp_excl_scan<uint32_t>((uint32_t)__popc(m), run);
+    if ((int)run == bb.ncand) {
+      while (m) {
+        const int bi = __ffs(m) - 1;
+        m &= m - 1;
+        cv[off] = __float_as_uint(Pw[base + bi]);
+        cj[off] = (uint16_t)(base + bi);
+        ++off;
+      }
+    }
+    __syncwarp();
+    if ((int)run != bb.ncand) slow = true;  // uniform (a warp total)
+    if (!slow && !comb_band_sorted(scratch, bb.ncand, lo_r, bb.cb, bw, bv, bj, bad)) slow = true;
+    __syncwarp();
+  }
+  if (slow) {
+    uint32_t bvu = 0u;
+    __syncwarp();
+    bad |= comb_band_exact(Pw, N, lo_r, hi_r, bw, hist, bvu, bj);
+    bv = __uint_as_float(bvu);
+    __syncwarp();
+  }
+  __syncwarp();
+
+  // ---- Eq. 8-10
+  const bool uniform = kM * cc.w_hi <= N - 1 - kD && N > kM * (2 * kD + 1);
+  float *nws = reinterpret_cast<float *>(scratch + CombFast::nw_off(N, cc.w_hi - cc.w_lo + 1));
+  float maxnw;
+  int maxi;
+  comb_nw_all<kM, kD>(rec, nws, cc, uniform, maxnw, maxi);
+  __syncwarp();
+  float best;
+  int bestw;
+  comb_best<kM, kD>(Pw, nws, cc, uniform, maxnw, maxi, bv, bj, best, bestw, bad);
+  out = comb_out(best, bestw, bad, out.log_sf, cc);
+  __syncwarp();
+  return out;
+}
+
+__device__ __forceinline__ CombOut comb_warp_fast(const float *Pw, const CombConst &cc,
+                                                  unsigned char *scratch) {
+  if (CombReg::fits(cc)) return comb_warp_fast_regs(Pw, cc, scratch);
+  return comb_warp_fast_smem(Pw, cc, scratch);
+}
+
+// Which comb variant a context uses: 0 = fast (N <= 1024, band <= 32; the
+// register or shared-memory form, chosen at run time), otherwise the generic
+// one with NW mask words per centre. A kernel that scores every pixel of one
+// context can instead take the fast form itself: 2 = register form, 3 =
+// shared-memory form (comb_fast_form).
 __host__ __device__ inline int comb_variant(const CombConst &cc) {
   if (cc.N <= CombFast::kMaxN && cc.bw <= CombFast::kMaxBand && cc.M * (2 * cc.d + 1) <= 32)
     return 0;
   return cc.bw <= 32 ? 1 : 8;
 }
 
-__host__ __device__ inline int comb_scratch_bytes(int N, int variant) {
-  return variant == 0 ? CombFast::bytes(N) : CombScratch::bytes(N, variant);
+__host__ __device__ inline int comb_fast_form(const CombConst &cc) {
+  return CombReg::fits(cc) ? 2 : 3;
+}
+
+__host__ __device__ inline int comb_scratch_bytes(const CombConst &cc, int variant) {
+  return (variant == 0 || variant == 2 || variant == 3)
+             ? CombFast::bytes(cc.N, cc.w_hi - cc.w_lo + 1)
+             : CombScratch::bytes(cc.N, variant);
 }
 
 // Eq. 7-11 for one pixel's spectrum Pw[0..N) in shared memory by the calling
-// warp; scratch: comb_scratch_bytes(N, NW) bytes (16-byte aligned).
+// warp; scratch: comb_scratch_bytes(cc, NW) bytes (16-byte aligned).
 template <int NW>
 __device__ __forceinline__ CombOut comb_warp(const float *Pw, const CombConst &cc,
                                              unsigned char *scratch) {
   if constexpr (NW == 0) return comb_warp_fast(Pw, cc, scratch);
+  else if constexpr (NW == 2) return comb_warp_fast_regs(Pw, cc, scratch);
+  else if constexpr (NW == 3) return comb_warp_fast_smem(Pw, cc, scratch);
   else return comb_warp_generic<NW>(Pw, cc, scratch);
 }
 

@@ -13,11 +13,11 @@ namespace ddhf {
 
 // The row is copied to shared memory with all of a lane's loads in flight at
 // once (16-byte loads when the rows are 16-byte aligned), then scored by
-// comb_warp. 4 warps per block; the fast variant is held to 64 registers so
-// that 8 blocks fit on an SM with its 6.9 KB of shared memory per warp at 750
-// bins.
+// comb_warp. 4 warps per block; the register form of the fast variant is held
+// to 80 registers (6 blocks, 24 warps per SM; its 7.4 KB of shared memory per
+// warp at 750 bins would allow 7), the shared-memory form to 64.
 template <int NW, bool CPLX>
-__global__ void __launch_bounds__(128, NW == 0 ? 8 : 1) k_comb(const float *__restrict__ P, int64_t ld, int64_t cap_px,
+__global__ void __launch_bounds__(128, NW == 2 ? 6 : (NW == 3 ? 8 : 1)) k_comb(const float *__restrict__ P, int64_t ld, int64_t cap_px,
                        const uint32_t *__restrict__ active, const uint64_t *__restrict__ counters,
                        CombConst cc, float *log_sf, float *snr, int32_t *f0, uint8_t *mask,
                        int warp_bytes, uint32_t *flags) {
@@ -109,10 +109,11 @@ template <bool CPLX>
 ddhf_status launch_comb_t(Ctx *c, const float *P, int64_t cap_px, float *log_sf, float *snr,
                           int32_t *f0, uint8_t *mask, cudaStream_t s, int slot, int64_t ld) {
   const Slot &sl = c->slots[slot];
-  const int variant = comb_variant(c->comb);
+  int variant = comb_variant(c->comb);
+  if (variant == 0) variant = comb_fast_form(c->comb);
   const int wpb = 4;
   const int warp_bytes = ((c->grid.n_bins * 4 + 15) & ~15) +
-                         ((comb_scratch_bytes(c->grid.n_bins, variant) + 15) & ~15);
+                         ((comb_scratch_bytes(c->comb, variant) + 15) & ~15);
   const size_t smem = (size_t)warp_bytes * wpb;
   DDHF_CUDA_TRY(c, cudaMemsetAsync(mask, 0, c->npx, s));
 #define DDHF_COMB_CASE(NWV)                                                                    \
@@ -130,7 +131,8 @@ ddhf_status launch_comb_t(Ctx *c, const float *P, int64_t cap_px, float *log_sf,
                                                   sl.active, sl.counters, c->comb, log_sf, snr, \
                                                   f0, mask, warp_bytes, c->flags);             \
   }
-  if (variant == 0) DDHF_COMB_CASE(0)
+  if (variant == 2) DDHF_COMB_CASE(2)
+  else if (variant == 3) DDHF_COMB_CASE(3)
   else if (variant == 1) DDHF_COMB_CASE(1)
   else DDHF_COMB_CASE(8)
 #undef DDHF_COMB_CASE

@@ -74,6 +74,35 @@ struct GridConst {
   float two_over_denom;
 };
 
+// The grid requirements of include/ddhf.h: a0 >= 0, da > 0, 0 < denom <
+// 2^31, 1 <= n_bins <= 16384, and the last A row's frequency (bin n_bins - 1
+// rounded up to a 32-bin row) below 2^32.
+inline bool grid_ok(const ddhf_grid *g) {
+  if (!g || g->a0 < 0 || g->da <= 0 || g->denom <= 0 || g->denom >= ((int64_t)1 << 31) ||
+      g->n_bins < 1 || g->n_bins > 16384)
+    return false;
+  return (double)g->a0 + (double)g->da * (g->n_bins - 1 + 31) < 4294967296.0;
+}
+
+// Residues and reduction constants of a valid grid (one derivation shared by
+// the context and the no-allocation entry point, so both evaluate the same
+// phases).
+inline GridConst make_grid_const(const ddhf_grid &g) {
+  GridConst k;
+  k.a0 = (uint64_t)g.a0;
+  k.da = (uint64_t)g.da;
+  k.denom = (uint64_t)g.denom;
+  k.barrett = ~0ull / (uint64_t)g.denom;
+  k.a0_mod = (uint64_t)g.a0 % (uint64_t)g.denom;
+  k.da_mod = (uint64_t)g.da % (uint64_t)g.denom;
+  k.da16_mod = ((uint64_t)g.da * 16ull) % (uint64_t)g.denom;
+  k.da32_mod = ((uint64_t)g.da * 32ull) % (uint64_t)g.denom;
+  k.N = g.n_bins;
+  k.nbr = (g.n_bins + 31) / 32;
+  k.two_over_denom = (float)(2.0 / (double)g.denom);
+  return k;
+}
+
 struct SlideState;  // sliding-window spectra (slide.cu)
 
 // Hybrid spectra (ndft_hybrid.cu): the grid rows a window needs, at most

@@ -435,7 +435,7 @@ int blocked_warp_bytes(const Ctx *c, bool fused, int NW, int *pw_offset) {
   const int partial = 3 * TB * 4 * 32 * 4;
   if (partial > scratch) scratch = partial;
   if (fused) {
-    int cb = comb_scratch_bytes(c->grid.n_bins, NW);
+    int cb = comb_scratch_bytes(c->comb, NW);
     if (cb > scratch) scratch = cb;
   }
   scratch = (scratch + 15) & ~15;

@@ -47,6 +47,7 @@ struct SoftArgs {
   float *S;                // forward output [n_px]
   const float *gS;         // backward input [n_px]
   float *g_f0;             // backward output [n_px]
+  float *g_f;              // backward output [n_px][n_h][2Q+1], nullable
   float *part;             // backward workspace [n_px][2 n_h]
   int backward;
   uint64_t barrett;        // floor((2^64-1) / 1e9)
@@ -162,6 +163,21 @@ __global__ void __launch_bounds__(256) k_softcomb(SoftArgs A) {
         }
       }
       S += wh * (Ac / Z) / Bv;
+      if (BWD && A.g_f) {
+        // per evaluation frequency: g dS/df_hq = g w_h G_hq P'(f_hq) / (Z_h B),
+        // written by lane q (every lane holds the reduced sums)
+        const float gs = A.gS[a];
+        float *out = A.g_f + (a * A.n_h + (h - 1)) * (int64_t)nq;
+#pragma unroll
+        for (int q = 0; q < 2 * kSoftMaxQ + 1; ++q) {
+          if (q < nq && lane == q) {
+            const float qd = __fmul_rn((float)(q - A.Q), A.delta_hz);
+            const float G = expf(-(qd * qd) / (2.f * sgm * sgm));
+            const float Pd = 2.f * (Fr[q] * Dr[q] + Fi[q] * Di[q]);
+            out[q] = gs * (wh * G * Pd / (Z * Bv));
+          }
+        }
+      }
       if (BWD) {
         g0 += wh * (float)h * (Ad / Z) / Bv;
         if (lane == 0) {
@@ -277,7 +293,7 @@ extern "C" ddhf_status ddhf_softcomb(ddhf_ctx *h, int64_t n_px, const uint32_t *
                                      double tau_c_us, const float *w, const float *sigma,
                                      const float *B, float *S, const float *grad_S,
                                      float *grad_f0, float *grad_w, float *grad_sigma,
-                                     ddhf_stream stream) {
+                                     float *grad_f, ddhf_stream stream) {
   if (!h) return DDHF_ERR_INVALID_ARG;
   Ctx *c = &h->c;
   if (!c->binned) {
@@ -320,6 +336,7 @@ extern "C" ddhf_status ddhf_softcomb(ddhf_ctx *h, int64_t n_px, const uint32_t *
   A.S = S;
   A.gS = grad_S;
   A.g_f0 = grad_f0;
+  A.g_f = bwd ? grad_f : nullptr;
   A.part = c->soft_part;  // [n_px][2 n_h] then the 2 n_h column sums
   A.backward = bwd;
   A.barrett = ~0ull / 1000000000ull;

@@ -76,6 +76,13 @@ class ddhf_box(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in ("x0", "y0", "x1", "y1", "n_px")]
 
 
+class ddhf_pipe_peaks(ctypes.Structure):
+    _fields_ = [("sm_count", ctypes.c_int32), ("sm_clock_max_mhz", ctypes.c_int32),
+                ("ffma_per_s", ctypes.c_double), ("ffma2_lane_per_s", ctypes.c_double),
+                ("sin_approx_per_s", ctypes.c_double), ("lg2_approx_per_s", ctypes.c_double),
+                ("elapsed_ms", ctypes.c_float * 4)]
+
+
 class ddhf_slide_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in (
         "t_end_us", "pushes", "rebuilds", "n_added", "n_dropped", "n_expired", "n_window",
@@ -110,10 +117,10 @@ SIGNATURES = {
     "ddhf_stage_times": (_I32, [_VP, ctypes.POINTER(ctypes.c_float)]),
     "ddhf_last_error": (ctypes.c_char_p, [_VP]),
     "ddhf_softcomb": (_I32, [_VP, _I64, _VP, _VP, _I32, _I32, ctypes.c_double, ctypes.c_double,
-                             _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+                             _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "ddhf_spectrum_median": (_I32, [_VP, _VP, _I64, _VP, _VP]),
     "ddhf_power_spectrum_noalloc": (_I32, [ctypes.POINTER(ddhf_grid), _VP, _VP, _I64, _VP, _I64,
-                                           _VP, _I64, _VP]),
+                                           _VP, _I64, _VP, _VP]),
     "ddhf_detect_batch_host": (_I32, [_VP, ctypes.POINTER(ddhf_window), _I32, _VP, _I32, _VP,
                                       _VP, _VP]),
     "ddhf_set_row_offset": (_I32, [_VP, _I32]),
@@ -126,6 +133,7 @@ SIGNATURES = {
     "ddhf_slide_spectra": (_I32, [_VP, _VP, _I64, _VP]),
     "ddhf_slide_detect": (_I32, [_VP, _VP, _I32, _VP, _VP, _VP]),
     "ddhf_slide_get_stats": (_I32, [_VP, ctypes.POINTER(ddhf_slide_stats)]),
+    "ddhf_measure_pipes": (_I32, [ctypes.POINTER(ddhf_pipe_peaks), _I32, _VP]),
 }
 
 _lib = None
@@ -356,20 +364,23 @@ def ddhf_stage_times(ctx):
 
 
 def ddhf_power_spectrum_noalloc(grid, offsets, ev, n_events, active, n_active, P, cap_px,
-                                stream=None):
+                                flags=None, stream=None):
     """Blocked-form spectra from a caller-owned per-pixel list; the library
-    allocates nothing (see include/ddhf.h for who needs this and its limits)."""
+    allocates nothing (see include/ddhf.h for who needs this and its limits).
+    flags: optional device int32 tensor of one element that receives the
+    DDHF_FLAG_* bits the call raised."""
     _check(load().ddhf_power_spectrum_noalloc(ctypes.byref(grid), _ptr(offsets), _ptr(ev),
                                               int(n_events), _ptr(active), int(n_active),
-                                              _ptr(P), int(cap_px), _stream(stream)))
+                                              _ptr(P), int(cap_px), _ptr(flags), _stream(stream)))
 
 
 def ddhf_softcomb(ctx, pixels, f0, n_h, Q, delta_hz, tau_c_us, w, sigma, B, S=None,
-                  grad_S=None, grad_f0=None, grad_w=None, grad_sigma=None, stream=None):
+                  grad_S=None, grad_f0=None, grad_w=None, grad_sigma=None, grad_f=None,
+                  stream=None):
     _check(load().ddhf_softcomb(ctx, int(pixels.numel()), _ptr(pixels), _ptr(f0), int(n_h), int(Q),
                                 float(delta_hz), float(tau_c_us), _ptr(w), _ptr(sigma), _ptr(B),
                                 _ptr(S), _ptr(grad_S), _ptr(grad_f0), _ptr(grad_w),
-                                _ptr(grad_sigma), _stream(stream)), ctx)
+                                _ptr(grad_sigma), _ptr(grad_f), _stream(stream)), ctx)
 
 
 def ddhf_spectrum_median(ctx, P, rows, median, stream=None):
@@ -401,6 +412,15 @@ class SoftComb(torch.autograd.Function):
         ddhf_softcomb(handle, pixels, f0c, wc.numel(), Q, delta_hz, tau_c_us, wc, sc, B,
                       grad_S=gS.contiguous(), grad_f0=g_f0, grad_w=g_w, grad_sigma=g_s)
         return g_f0, g_w, g_s, None, None, None, None, None, None
+
+
+def ddhf_measure_pipes(iters=1 << 16, stream=None):
+    """Pipe throughput of the current device (dict of the struct's fields)."""
+    out = ddhf_pipe_peaks()
+    _check(load().ddhf_measure_pipes(ctypes.byref(out), int(iters), _stream(stream)))
+    d = {k: getattr(out, k) for k, _ in ddhf_pipe_peaks._fields_ if k != "elapsed_ms"}
+    d["elapsed_ms"] = list(out.elapsed_ms)
+    return d
 
 
 def ddhf_get_stats(ctx, raise_on_flags=True):
