@@ -52,7 +52,6 @@ UNIT = "terms/s"
 WORKLOAD = ("C3: {W}x{H}, 8 consecutive 30 ms windows x 4 streams per step, Pareto(1.5) "
             "per-pixel counts capped at 20k, 3 drones; grid 0-1498 Hz step 2 Hz (750 bins); "
             "Table 2 parameters")
-SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 OPS_PER_TERM = 3  # FP32 FMA-pipe lane-ops per term of the blocked three-multiplication form
 # DRAM bytes (read + write) per active pixel of one launch, from one ncu capture
 # of a kernel on a 640x360 window of the same recipe, scaled to a launch by its
@@ -152,6 +151,43 @@ def slide_leg(wins, W, H, grid, torch, ddhf, hop_us=3750, rebuild_every=64, cap_
         push_state_gbs=(st["last_pixels"] * nbins * 16 + delta / n * 8) / (np.median(push) * 1e-3)
         / 1e9,
         unit="ms per hop (CUDA events); delta terms = (events in + events out) x bins")
+
+
+def latency_sweep(means, W, H, grid, tuning, torch, ddhf, replays=100, seed=1003):
+    """One 1280x720 window of the C3 recipe at lower event densities (stream 0,
+    window 0, the Pareto counts scaled to `mean` events per pixel): the
+    graph-replayed detection timed replay by replay. Gives the largest event
+    count whose median latency is under 1 ms."""
+    rows = []
+    for m in means:
+        sc = synth.config3_window(0, 0, seed=seed, W=W, H=H, mean_per_px=m)
+        c = ddhf.Context(W, H, grid, max_events=max(sc.n, 1), max_windows=1)
+        c.set_tuning(**{k: v for k, v in tuning.items() if k != "how"})
+        d = ddhf.events_to_device(sc)
+        wl = [(d[0], d[1], d[2], d[3], sc.n, sc.t0, sc.window_us)]
+        bx = torch.empty((256, 5), dtype=torch.int32, device="cuda")
+        nb = torch.zeros(1, dtype=torch.int32, device="cuda")
+        for _ in range(5):
+            ddhf.ddhf_detect_batch(c.h, wl, bx, 256, nb, None, use_graph=True)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(replays)]
+        for a, b in evs:
+            a.record()
+            ddhf.ddhf_detect_batch(c.h, wl, bx, 256, nb, None, use_graph=True)
+            b.record()
+        torch.cuda.synchronize()
+        lt = np.array([a.elapsed_time(b) for a, b in evs])
+        st = c.stats()
+        c.close()
+        q25, q50, q75, q95 = np.percentile(lt, [25, 50, 75, 95])
+        rows.append(dict(mean_per_px=m, events=int(sc.n), active_pixels=int(st["n_active"]),
+                         terms=int(st["terms"]), median_ms=float(q50), iqr_ms=float(q75 - q25),
+                         p95_ms=float(q95)))
+    under = [r["events"] for r in rows if r["median_ms"] < 1.0]
+    return dict(window=f"{W}x{H}, 30 ms, C3 recipe (stream 0, window 0) at lower densities; "
+                       f"{replays} graph replays each",
+                points=rows, largest_events_under_1ms=max(under) if under else None)
 
 
 def rank_seed(rank: int) -> int:
@@ -284,31 +320,81 @@ def oracle_sample(b, W, H, grid, n_pixels, seed=5):
     return terms, time.perf_counter() - t_0, int(pix.size)
 
 
+def _oracle_chunk(args):
+    """One worker's share of the CPU baseline: the oracle, as it stands, on a
+    list of active pixels (Eq. 6-11 per pixel), given as a one-row sensor that
+    holds just those pixels' events (so that little is sent to the worker)."""
+    import oracle
+    npx, b, grid = args
+    t_0 = time.perf_counter()
+    oracle.classify(npx, 1, b, grid)
+    return time.perf_counter() - t_0
+
+
+def _pixel_subset(b, pix):
+    """The events of pixels `pix` of a binned window as a one-row sensor."""
+    cnt = b["counts"][pix]
+    offs = np.zeros(pix.size + 1, np.int64)
+    offs[1:] = np.cumsum(cnt)
+    sel = np.concatenate([np.arange(b["offsets"][k], b["offsets"][k + 1]) for k in pix])
+    return dict(offsets=offs, tau=b["tau"][sel], pol=b["pol"][sel], counts=cnt)
+
+
+def oracle_all_cores(b, W, H, grid, n_pixels, seed=5, procs=None):
+    """The oracle on a seeded sample of active pixels split over every host
+    core (one spawned worker per core, each a single-threaded oracle call).
+    Returns (terms, wall seconds, pixels, workers)."""
+    procs = procs or os.cpu_count() or 1
+    act = np.flatnonzero(b["counts"] >= 6)
+    rng = np.random.default_rng(seed)
+    pix = np.sort(rng.choice(act, size=min(n_pixels, act.size), replace=False))
+    terms = int(b["counts"][pix].sum()) * grid[3]
+    chunks = [c for c in np.array_split(pix, procs) if c.size]
+    jobs = [(c.size, _pixel_subset(b, c), grid) for c in chunks]
+    with mp.get_context("spawn").Pool(processes=len(chunks)) as pool:
+        pool.map(_oracle_chunk, [(1, _pixel_subset(b, chunks[0][:1]), grid)] * len(chunks))
+        t_0 = time.perf_counter()
+        pool.map(_oracle_chunk, jobs, chunksize=1)
+        wall = time.perf_counter() - t_0
+    return terms, wall, int(pix.size), len(chunks)
+
+
 def run_reference(args):
-    """The oracle timed on the host cores on bounded samples of the workload."""
+    """The oracle timed on the host cores on bounded samples of the workload:
+    each step scores a seeded sample of active pixels of one C3 window with
+    one spawned single-threaded oracle worker per host core."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     sc = synth.config3_window(0, 0)
     b = oracle_bin((sc.x, sc.y, sc.t, sc.p, sc.t0, sc.window_us, sc.n), sc.W, sc.H)
-    per_step = 60
-    for i in range(args.warmup):
-        oracle_sample(b, sc.W, sc.H, sc.grid, 8, seed=100 + i)
+    procs = os.cpu_count() or 1
+    per_step = 40 * procs
+    act = np.flatnonzero(b["counts"] >= 6)
     tot_terms, tot_s = 0, 0.0
-    for i in range(args.steps):
-        tr, s, _ = oracle_sample(b, sc.W, sc.H, sc.grid, per_step, seed=1000 + i)
-        tot_terms += tr
-        tot_s += s
+    with mp.get_context("spawn").Pool(processes=procs) as pool:
+        for i in range(args.warmup + args.steps):
+            rng = np.random.default_rng(1000 + i)
+            pix = np.sort(rng.choice(act, size=min(per_step, act.size), replace=False))
+            jobs = [(c.size, _pixel_subset(b, c), sc.grid)
+                    for c in np.array_split(pix, procs) if c.size]
+            t_0 = time.perf_counter()
+            pool.map(_oracle_chunk, jobs, chunksize=1)
+            dt = time.perf_counter() - t_0
+            if i >= args.warmup:
+                tot_terms += int(b["counts"][pix].sum()) * sc.grid[3]
+                tot_s += dt
     v = tot_terms / tot_s
     sample = (f"per step {per_step} seeded random active pixels of window 0 of stream 0 "
-              f"(1280x720, 750 bins): FP64 NDFT + SF + comb, single thread")
+              f"(1280x720, 750 bins), split over {procs} spawned single-threaded oracle "
+              f"workers: FP64 NDFT + SF + comb")
     line = dict(impl="reference", metric=METRIC, value=v, unit=UNIT, n_gpus=args.gpus,
                 steps=args.steps, warmup=args.warmup, ms_per_step=1e3 * tot_s / args.steps,
                 higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
                 data="synthetic",
                 config=dict(workload=WORKLOAD.format(W=1280, H=720),
                             sample="oracle on seeded pixel samples of window 0 of stream 0"),
-                cpu_baseline=dict(value=v, unit=UNIT, cores=1, kind="oracle", sample=sample),
+                cpu_baseline=dict(value=v, unit=UNIT, cores=procs, kind="oracle", sample=sample),
                 e2e=dict(value=v, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
 
@@ -329,6 +415,8 @@ def main():
                     help="JSON dict of ddhf_tuning fields to use instead of the autotuner")
     ap.add_argument("--procs", type=int, default=int(os.environ.get("DDHF_GEN_PROCS", "16")))
     ap.add_argument("--no-latency", action="store_true", help="skip the one-window latency")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the one-window latency at lower event densities")
     ap.add_argument("--no-softcomb", action="store_true", help="skip the soft-comb timing")
     ap.add_argument("--no-slide", action="store_true", help="skip the sliding-window timing")
     ap.add_argument("--no-forms", action="store_true",
@@ -381,7 +469,9 @@ def main():
     wl = [(d[0], d[1], d[2], d[3], w[6], w[4], w[5]) for d, w in zip(dev, wins)]
     boxes = torch.empty((nwin * cap, 5), dtype=torch.int32, device="cuda")
     nbox = torch.zeros(nwin, dtype=torch.int32, device="cuda")
-    ddhf.ddhf_enable_stage_timing(ctx.h, True)
+    # pipe throughput of this device (the NDFT roofline's denominator), before
+    # the workload's first launch
+    peaks = ddhf.ddhf_measure_pipes()
     tuning, tune_note = ddhf.ddhf_get_tuning(ctx.h), "default"
     if args.tuning:
         ctx.set_tuning(**json.loads(args.tuning))
@@ -414,16 +504,9 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    fused_ms, bin_ms, box_ms, spec_ms, comb_ms = [], [], [], [], []
     e0.record()
     for _ in range(args.steps):
         step()
-        b_ms, f_ms, x_ms, sp_ms, cb_ms = ddhf.ddhf_stage_times(ctx.h)  # waits for this step
-        bin_ms.append(b_ms)
-        fused_ms.append(f_ms)
-        box_ms.append(x_ms)
-        spec_ms.append(sp_ms)
-        comb_ms.append(cb_ms)
     e1.record()
     torch.cuda.synchronize()
     if dist:
@@ -433,6 +516,22 @@ def main():
     ms_step = ms / args.steps
     value = job_throughput(terms_step, world, args.steps, ms)
     st = ctx.stats()
+    # ------------------------------------------------------------ per-stage breakdown
+    # after the timed region: the same step with CUDA events around each stage
+    # (a separately captured graph; each step is read back before the next)
+    ddhf.ddhf_enable_stage_timing(ctx.h, True)
+    step()
+    torch.cuda.synchronize()
+    fused_ms, bin_ms, box_ms, spec_ms, comb_ms = [], [], [], [], []
+    for _ in range(3):
+        step()
+        b_ms, f_ms, x_ms, sp_ms, cb_ms = ddhf.ddhf_stage_times(ctx.h)
+        bin_ms.append(b_ms)
+        fused_ms.append(f_ms)
+        box_ms.append(x_ms)
+        spec_ms.append(sp_ms)
+        comb_ms.append(cb_ms)
+    ddhf.ddhf_enable_stage_timing(ctx.h, False)
     # ------------------------------------------------------------ e2e from pinned host memory
     e2e = None
     if not args.no_e2e:
@@ -488,6 +587,11 @@ def main():
                    events=int(wins[0][6]), replays=len(lt), median_ms=float(q50),
                    iqr_ms=float(q75 - q25), p95_ms=float(q95), min_ms=float(lt.min()))
         lc.close()
+    # ------------------------------------------------------------ latency at lower densities
+    sweep = None
+    if not args.no_sweep and rank == 0:
+        sweep = latency_sweep((1.0, 2.0, 3.0, 5.0, 10.0), W, H, grid, tuning, torch, ddhf,
+                              replays=args.latency_replays)
     # ------------------------------------------------------------ spectrum forms, one window
     # window 0 alone through ddhf_power_spectrum: the blocked kernel on every
     # active pixel (the FMA-pipe roofline of that kernel, without the hybrid
@@ -626,13 +730,19 @@ def main():
     # ------------------------------------------------------------ CPU baseline (oracle)
     cpu = None
     if rank == 0 and world == 1 and not args.no_oracle:
-        tr, secs, npix = oracle_sample(oracle_bin(wins[0], W, H), W, H, grid, 1200)
-        cpu = dict(value=tr / secs, unit=UNIT, cores=1, kind="oracle",
-                   sample=f"{npix} seeded random active pixels of window 0 of stream 0: "
-                          f"FP64 NDFT + SF + comb (Eq. 6-11), {secs:.1f} s single-threaded")
+        b0 = oracle_bin(wins[0], W, H)
+        ncores = os.cpu_count() or 1
+        tr, secs, npix, nw = oracle_all_cores(b0, W, H, grid, 400 * ncores)
+        tr1, secs1, npix1 = oracle_sample(b0, W, H, grid, 600, seed=6)
+        cpu = dict(value=tr / secs, unit=UNIT, cores=nw, kind="oracle",
+                   sample=f"{npix} seeded random active pixels of window 0 of stream 0, split "
+                          f"over {nw} spawned single-threaded oracle workers (one per host "
+                          f"core): FP64 NDFT + SF + comb (Eq. 6-11), {secs:.1f} s wall",
+                   one_core=dict(value=tr1 / secs1, pixels=npix1, seconds=secs1),
+                   host_cores=ncores)
     f_avg = statistics.mean(fused_ms)
     fused_mode = statistics.mean(spec_ms) == 0.0
-    peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    peak = peaks["ffma2_lane_per_s"] / 1e12
     hybrid_on = not fused_mode and int(tuning.get("hybrid_min", 0)) > 0
     if fused_mode:
         ndft_ms, kern = f_avg, "fused blocked NDFT + SF + comb kernel (k_blocked<TB,NW,1>)"
@@ -660,7 +770,8 @@ def main():
                      traffic_note=None if tr_ndft is not None else TRAFFIC_NOTE,
                      kernel=kern, launches_per_step=ndft_launches, launch_ms=ndft_launch_ms,
                      kernel_ms_per_step=ndft_ms, share_of_step=ndft_ms / ms_step,
-                     peak_source="derived: 152 SMs x 128 FP32 lanes x 2070 MHz",
+                     peak_source=("measured: ddhf_measure_pipes, paired FP32 FMA (f32x2) "
+                                  f"chains on {peaks['sm_count']} SMs"),
                      ops="3 FP32 FMA-pipe lane-ops per term (three-multiplication complex "
                          "product)")
     roof_comb = None
@@ -698,11 +809,13 @@ def main():
                                            spectra=statistics.mean(spec_ms),
                                            comb=statistics.mean(comb_ms),
                                            labels_boxes=statistics.mean(box_ms)),
-                    stage_note=("per-stage CUDA-event durations; with the overlap tuning the "
-                                "comb of one window runs beside the binning and spectra of the "
-                                "next, so stages overlap in time and their sum exceeds the step"
-                                if int(tuning.get("overlap", 0)) else
-                                "per-stage CUDA-event durations, stages in sequence"),
+                    stage_note=("per-stage CUDA-event durations over 3 extra steps after the "
+                                "timed region (a graph with event nodes, read back after each "
+                                "step); " +
+                                ("with the overlap tuning the comb of one window runs beside "
+                                 "the binning and spectra of the next, so stages overlap in "
+                                 "time and their sum exceeds the step"
+                                 if int(tuning.get("overlap", 0)) else "stages in sequence")),
                     l2="inputs 8.3 GB per step, larger than L2; no flush",
                     tuning=dict(tuning, how=tune_note),
                     parallelism=f"replicas x{world}"),
@@ -711,6 +824,10 @@ def main():
         roofline_comb=roof_comb,
         e2e=e2e,
         window_latency=lat,
+        latency_sweep=sweep,
+        peaks=dict(peaks, unit="per second, whole device",
+                   how="ddhf_measure_pipes: 8 independent chains per thread, 8 blocks of "
+                       "256 threads per SM, CUDA events"),
         softcomb=softc,
         spectrum_forms=forms,
         slide=slide,

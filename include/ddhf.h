@@ -183,9 +183,11 @@ typedef struct {
  *                   allocated when this is first set); 0 turns it off. The
  *                   fused kernel ignores it.
  * Defaults: heavy_min 1024, 4 warps per block, blocks_per_sm 0, rows_per_lane
- * 0, fuse 0 (the unfused path needs the context's spectrum buffer, present
- * when n_bins <= 4096; larger grids always run fused), overlap 0,
- * hybrid_min 0.
+ * 0, fuse 0, overlap 0, hybrid_min 0. The unfused path needs the context's
+ * spectrum buffer of W*H rows of n_bins floats, allocated by ddhf_create (for
+ * more than 4096 bins only when the device has room: without it detection
+ * runs fused, and returns DDHF_ERR_UNSUPPORTED when the fused kernel's
+ * per-warp shared memory does not fit an SM).
  * Different tunings give spectra that agree within the FP32 rounding of the
  * summation order; each tuning is deterministic. */
 typedef struct {
@@ -277,7 +279,11 @@ ddhf_status ddhf_power_spectrum(ddhf_ctx *ctx, int32_t form, float *P, int64_t c
                                 ddhf_stream stream);
 
 /* Eq. 7-11 on spectra P laid out as ddhf_power_spectrum writes them (rows in
- * active-list order of slot 0). Per active pixel a: log_sf[a] = ln SF;
+ * active-list order of slot 0), for any grid of the context: rows are scored
+ * in shared memory, or, for the largest grids, where they are in P (then
+ * only the comb's scratch needs shared memory: DDHF_ERR_UNSUPPORTED when
+ * even that does not fit, which takes both many bins and a median band of
+ * more than 32 ranks, M (2d+1) > 30). Per active pixel a: log_sf[a] = ln SF;
  * snr[a] = max_w SNR_M(w) and f0_bin[a] = its first maximising bin w when
  * SF <= tau_sf (else 0 and -1); mask[W*H] (uint8, zeroed by the call) gets 1
  * at rotor pixels (SF <= tau_sf and snr >= tau_comb). log_sf, snr and f0_bin

@@ -401,7 +401,16 @@ ddhf_status ddhf_create(int32_t W, int32_t H, const ddhf_grid *grid, const ddhf_
   A(c->flags, 1);
   A(c->soft_part, 16 * npx + 16);
   c->pbuf_ld = ((int64_t)grid->n_bins + 3) & ~(int64_t)3;  // 16-byte aligned rows
-  if (grid->n_bins <= 4096) A(c->pbuf, npx * c->pbuf_ld);
+  if (grid->n_bins <= 4096) {
+    A(c->pbuf, npx * c->pbuf_ld);
+  } else if (st == DDHF_OK) {
+    // a large grid's spectrum buffer (W*H rows of n_bins floats) is optional:
+    // without it detection runs the fused kernel
+    if (cudaMalloc(&c->pbuf, (size_t)npx * c->pbuf_ld * sizeof(float)) != cudaSuccess) {
+      c->pbuf = nullptr;
+      cudaGetLastError();
+    }
+  }
 #undef A
   if (st == DDHF_OK) {
     cudaMemset(c->qctl, 0, 16 * sizeof(uint32_t));
@@ -644,7 +653,6 @@ ddhf_status ddhf_detect(ddhf_ctx *h, const int16_t *x, const int16_t *y, const i
   DDHF_TRY(check_window(c, x, y, t_us, p, n, window_us));
   if (!n_boxes_dev || cap < 0 || (cap > 0 && !boxes))
     return fail(c, DDHF_ERR_INVALID_ARG, "bad box arguments");
-  if (c->grid.n_bins > 4096) return fail(c, DDHF_ERR_UNSUPPORTED, "fused path needs n_bins <= 4096");
   cudaStream_t s = (cudaStream_t)stream;
   c->last_stream = s;
   ddhf_window w{x, y, t_us, p, n, t0_us, window_us};
@@ -662,7 +670,6 @@ ddhf_status ddhf_detect_batch(ddhf_ctx *h, const ddhf_window *wins, int32_t n_wi
     return fail(c, DDHF_ERR_INVALID_ARG, "n_windows out of [1, max_windows]");
   if (!n_boxes_dev || cap < 0 || (cap > 0 && !boxes))
     return fail(c, DDHF_ERR_INVALID_ARG, "bad box arguments");
-  if (c->grid.n_bins > 4096) return fail(c, DDHF_ERR_UNSUPPORTED, "fused path needs n_bins <= 4096");
   for (int w = 0; w < n_windows; ++w)
     DDHF_TRY(check_window(c, wins[w].x, wins[w].y, wins[w].t_us, wins[w].p, wins[w].n,
                           wins[w].window_us));

@@ -13,19 +13,21 @@ namespace ddhf {
 
 // The row is copied to shared memory with all of a lane's loads in flight at
 // once (16-byte loads when the rows are 16-byte aligned), then scored by
-// comb_warp. 4 warps per block; the register form of the fast variant is held
+// comb_warp; with spec_smem = 0 (the generic comb on a spectrum too large for
+// shared memory, real input only) comb_warp reads the row in global memory
+// and shared memory holds its scratch alone. 4 warps per block; the register form of the fast variant is held
 // to 80 registers (6 blocks, 24 warps per SM; its 7.4 KB of shared memory per
 // warp at 750 bins would allow 7), the shared-memory form to 64.
 template <int NW, bool CPLX>
 __global__ void __launch_bounds__(128, NW == 2 ? 6 : (NW == 3 ? 8 : 1)) k_comb(const float *__restrict__ P, int64_t ld, int64_t cap_px,
                        const uint32_t *__restrict__ active, const uint64_t *__restrict__ counters,
                        CombConst cc, float *log_sf, float *snr, int32_t *f0, uint8_t *mask,
-                       int warp_bytes, uint32_t *flags) {
+                       int warp_bytes, int spec_smem, uint32_t *flags) {
   extern __shared__ float4 smem4[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned char *base = reinterpret_cast<unsigned char *>(smem4) + warp * warp_bytes;
   float *Pw = reinterpret_cast<float *>(base);
-  unsigned char *scratch = base + ((cc.N * 4 + 15) & ~15);
+  unsigned char *scratch = base + (spec_smem ? ((cc.N * 4 + 15) & ~15) : 0);
   const int64_t n_active = (int64_t)counters[2];
   const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -36,12 +38,18 @@ __global__ void __launch_bounds__(128, NW == 2 ? 6 : (NW == 3 ? 8 : 1)) k_comb(c
   const int row_floats = CPLX ? 2 * N : N;
   for (int64_t a = wid; a < n_active && a < cap_px; a += nwarps) {
     const float *row = P + (CPLX ? (int64_t)active[a] : a) * ldf;
-    if (vec && lane == 0 && a + nwarps < n_active && a + nwarps < cap_px) {
-      // the warp's next row into L2 while this one is scored
-      const float *nxt = P + (CPLX ? (int64_t)active[a + nwarps] : a + nwarps) * ldf;
-      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(nxt),
-                   "r"((uint32_t)(((row_floats + 3) / 4) * 16))
-                   : "memory");
+    if (!CPLX && !spec_smem) {
+      // a spectrum too large for shared memory is scored where it is
+      CombOut o = comb_warp<NW>(row, cc, scratch);
+      if (lane == 0) {
+        if (o.bad) atomicOr(flags, DDHF_FLAG_INTERNAL);
+        if (log_sf) log_sf[a] = o.log_sf;
+        if (snr) snr[a] = o.snr;
+        if (f0) f0[a] = o.w;
+        mask[active[a]] = o.rotor;
+      }
+      __syncwarp();
+      continue;
     }
     if (vec) {
       const float4 *r4 = reinterpret_cast<const float4 *>(row);
@@ -111,9 +119,24 @@ ddhf_status launch_comb_t(Ctx *c, const float *P, int64_t cap_px, float *log_sf,
   const Slot &sl = c->slots[slot];
   int variant = comb_variant(c->comb);
   if (variant == 0) variant = comb_fast_form(c->comb);
-  const int wpb = 4;
-  const int warp_bytes = ((c->grid.n_bins * 4 + 15) & ~15) +
-                         ((comb_scratch_bytes(c->comb, variant) + 15) & ~15);
+  // 4 warps per block with the spectrum in shared memory when it fits; large
+  // spectra (the generic comb) take fewer warps per block, then leave the
+  // spectrum in global memory
+  int max_smem = 0;
+  DDHF_CUDA_TRY(c, cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin,
+                                          c->device));
+  const int scratch_b = (comb_scratch_bytes(c->comb, variant) + 15) & ~15;
+  const int spec_b = (c->grid.n_bins * 4 + 15) & ~15;
+  int wpb = 4, spec_smem = 1;
+  while (wpb > 1 && (spec_b + scratch_b) * wpb > max_smem) wpb >>= 1;
+  if ((spec_b + scratch_b) * wpb > max_smem) {
+    spec_smem = 0;
+    if (CPLX || scratch_b > max_smem) {
+      c->last_error = "comb scratch does not fit in shared memory for this grid and comb";
+      return DDHF_ERR_UNSUPPORTED;
+    }
+  }
+  const int warp_bytes = (spec_smem ? spec_b : 0) + scratch_b;
   const size_t smem = (size_t)warp_bytes * wpb;
   DDHF_CUDA_TRY(c, cudaMemsetAsync(mask, 0, c->npx, s));
 #define DDHF_COMB_CASE(NWV)                                                                    \
@@ -129,7 +152,7 @@ ddhf_status launch_comb_t(Ctx *c, const float *P, int64_t cap_px, float *log_sf,
     }                                                                                          \
     kern<<<c->num_sms * occ, wpb * 32, smem, s>>>(P, ld > 0 ? ld : c->grid.n_bins, cap_px,     \
                                                   sl.active, sl.counters, c->comb, log_sf, snr, \
-                                                  f0, mask, warp_bytes, c->flags);             \
+                                                  f0, mask, warp_bytes, spec_smem, c->flags);  \
   }
   if (variant == 2) DDHF_COMB_CASE(2)
   else if (variant == 3) DDHF_COMB_CASE(3)

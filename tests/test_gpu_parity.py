@@ -12,13 +12,17 @@ import pytest
 import torch
 
 import oracle
+import oracle_margins
 from paper_2603_08386_gb300 import ddhf, synth
 
 pytestmark = pytest.mark.gpu
 
 TOL_SPEC = 1e-4      # max_j |P_gpu - P_oracle| <= TOL_SPEC * max_j P_oracle, per pixel
-SF_MARGIN = 1e-4     # |ln SF - ln tau_sf| below this: decision not compared
-SNR_MARGIN = 1e-3    # |SNR / tau_comb - 1| below this: decision not compared
+# the SF decision on a given FP32 spectrum is compared with the FP64 oracle's
+# on the same spectrum wherever |ln SF - ln tau_sf| exceeds this (the FP32
+# arithmetic of Eq. 7); against the oracle's own FP64 spectrum the margins
+# also take the spectrum's difference into account (oracle_margins)
+SF_MARGIN = 1e-5
 D9 = synth.HZ_DENOM
 
 
@@ -269,43 +273,35 @@ def test_boxes_cap_and_hand_cases():
 
 # ------------------------------------------------------------------ whole window
 
-def margins_ok(oc, a_idx):
-    ln_tau = math.log(0.89)
-    lo = oc["log_sf"][a_idx]
-    if abs(lo - ln_tau) <= SF_MARGIN:
-        return False
-    if lo <= ln_tau and abs(oc["snr"][a_idx] / 1.5 - 1.0) <= SNR_MARGIN:
-        return False
-    return True
-
-
 def test_detect_c1_matches_oracle():
+    # C1 with Table 2's values: the FP64 oracle's rotor bit of every active
+    # pixel outside its margins, the boxes always against the oracle's
+    # segmentation of the GPU mask, and against the oracle's own boxes when
+    # no pixel is inside a margin
     s = synth.config1()
-    o = oracle.detect(s.W, s.H, s.events(), s.t0, s.window_us, s.grid)
-    oc = o["classified"]
+    prm = dict(tau_sf=0.89, tau_comb=1.5, M=4, d=3, h_min=4, A_min=147, alpha=19.05)
     c = ctx_for(s)
     x, y, t, p = ddhf.events_to_device(s)
     bx, nb, mask = c.detect(x, y, t, p, s.t0, s.window_us, cap=256, want_mask=True)
     sc = c.scores()
+    P32 = c.power_spectrum("blocked").cpu().numpy()
     c.stats()
     c.close()
-    act = sc["active"].cpu().numpy()
-    np.testing.assert_array_equal(act, oc["active"])
+    b = oracle_bin(s)
+    act = sc["active"].cpu().numpy().astype(np.int64)
+    np.testing.assert_array_equal(act, np.flatnonzero(b["counts"] >= 6))
     gm = mask.cpu().numpy()
-    ok = np.array([margins_ok(oc, i) for i in range(len(act))])
-    assert ok.mean() > 0.99
-    np.testing.assert_array_equal(gm[act[ok]], oc["mask"][act[ok]])
-    lsf = sc["log_sf"].cpu().numpy()
-    np.testing.assert_allclose(lsf, oc["log_sf"], atol=1e-4)
-    f0 = sc["f0_bin"].cpu().numpy()
-    rot = (oc["mask"][act] == 1) & ok
-    assert (f0[rot] == oc["w"][rot]).mean() > 0.98
-    if ok.all():
-        n = int(nb.item())
-        np.testing.assert_array_equal(bx[:n].cpu().numpy(), o["boxes"])
-    # the drone is found: a box covers its rotor pixels
-    dk = s.drones[0]["keys"]
-    assert gm[dk].mean() > 0.5
+    n = int(nb.item())
+    np.testing.assert_array_equal(bx[:n].cpu().numpy(),
+                                  oracle_margins.segment(gm, s.W, s.H, 147, 19.05, cap=256))
+    rot, close = oracle_margins.decisions(b, act, P32, s.grid, prm)
+    assert close.mean() < 0.01
+    np.testing.assert_array_equal(gm[act[~close]], rot[~close].astype(np.uint8))
+    if not close.any():
+        om = np.zeros(s.W * s.H, np.uint8)
+        om[act[rot]] = 1
+        np.testing.assert_array_equal(bx[:n].cpu().numpy(),
+                                      oracle_margins.segment(om, s.W, s.H, 147, 19.05, cap=256))
 
 
 @pytest.mark.parametrize("nb,step", [(750, 2), (2000, 1)])
@@ -435,3 +431,76 @@ def test_c3_window_full_size_sampled():
         assert err <= TOL_SPEC, (a, counts[a], err)
     c.stats()
     c.close()
+
+
+# ------------------------------------------------------------------ large grids
+
+@pytest.mark.parametrize("N,n_px", [(10_000, 8), (16_384, 3)])
+def test_comb_large_grid_bit_exact(N, n_px):
+    # the generic comb on the largest grids the header allows (C5's 10,000
+    # bins: spectrum and scratch in shared memory, one warp per block; 16,384:
+    # the row is scored where it is in global memory), against the oracle's
+    # FP32 restatement; rows with harmonic combs, noise, ties and zeros
+    params = ddhf.default_params(n_min=1)
+    s = synth.Scene(W=n_px, H=1, t0=0, window_us=100, x=np.arange(n_px).astype(np.int16),
+                    y=np.zeros(n_px, np.int16), t=np.zeros(n_px, np.int64),
+                    p=np.ones(n_px, np.int8), grid=synth.hz_grid(0, 1, N))
+    c = ctx_for(s, params)
+    x, y, t, p = ddhf.events_to_device(s)
+    c.bin_events(x, y, t, p, 0, 100)
+    Pn = synth.synthetic_spectra(n_px, N, seed=N)
+    out = c.comb_score(torch.from_numpy(Pn).cuda())
+    c.stats()
+    c.close()
+    lsf = out["log_sf"].cpu().numpy()
+    snr = out["snr"].cpu().numpy()
+    f0 = out["f0_bin"].cpu().numpy()
+    ln_tau = np.float32(math.log(0.89))
+    scored = 0
+    for a in range(n_px):
+        lo = oracle.log_sf(Pn[a].astype(np.float64))
+        assert abs(lsf[a] - lo) <= 1e-4 * max(1.0, abs(lo)), (a, lsf[a], lo)
+        if lsf[a] <= ln_tau:
+            s32, w32 = oracle.comb_f32(Pn[a])
+            assert w32 == f0[a], (a, w32, f0[a])
+            assert np.float32(s32).view(np.uint32) == np.float32(snr[a]).view(np.uint32)
+            scored += 1
+        else:
+            assert f0[a] == -1 and snr[a] == 0
+    assert scored >= 1
+
+
+def test_detect_large_grid():
+    # detection on C5's grid (0.5 Hz steps, 10,000 bins): the unfused path
+    # equals the spectrum + comb calls bit for bit, spectra match the FP64
+    # oracle and sampled scores match the oracle's FP32 comb on them
+    s = synth.small_scene(81, W=12, H=10, n_noise=6_000, drone_px=30, f0_hz=150.0,
+                          grid=synth.hz_grid(0, 0.5, 10_000))
+    c = ctx_for(s)
+    x, y, t, p = ddhf.events_to_device(s)
+    bx, nb, mask = c.detect(x, y, t, p, s.t0, s.window_us, want_mask=True)
+    sc = c.scores()
+    P = c.power_spectrum("blocked")
+    out = c.comb_score(P)
+    st = c.stats()
+    c.close()
+    assert st["n_active"] > 20
+    assert torch.equal(out["mask"], mask)
+    assert torch.equal(out["f0_bin"], sc["f0_bin"])
+    assert torch.equal(out["snr"].view(torch.int32), sc["snr"].view(torch.int32))
+    o = oracle_bin(s)
+    act = sc["active"].cpu().numpy()
+    Ph = P.cpu().numpy()
+    lsf = sc["log_sf"].cpu().numpy()
+    snr = sc["snr"].cpu().numpy()
+    f0 = sc["f0_bin"].cpu().numpy()
+    ln_tau = np.float32(math.log(0.89))
+    for a in np.linspace(0, len(act) - 1, 3).astype(int):
+        k = act[a]
+        o0, o1 = o["offsets"][k], o["offsets"][k + 1]
+        ref = oracle.ndft(o["tau"][o0:o1], o["pol"][o0:o1], *s.grid)
+        assert np.abs(Ph[a].astype(np.float64) - ref).max() <= TOL_SPEC * ref.max()
+        if lsf[a] <= ln_tau:
+            s32, w32 = oracle.comb_f32(Ph[a])
+            assert w32 == f0[a]
+            assert np.float32(s32).view(np.uint32) == np.float32(snr[a]).view(np.uint32)

@@ -14,13 +14,12 @@ import pytest
 import torch
 
 import oracle
+import oracle_margins
 from paper_2603_08386_gb300 import ddhf, synth
 
 pytestmark = pytest.mark.gpu
 
 TOL_SPEC = 1e-4
-SF_MARGIN = 1e-4
-SNR_MARGIN = 1e-3
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -240,20 +239,23 @@ def test_slide_detect_matches_oracle():
         bx, nb, mask = c.slide_detect(cap=256, want_mask=True)
         sc = c.scores()
         x, y, t, p = pu.window()
-        o = oracle.detect(s.W, s.H, dict(x=x, y=y, t=t, p=p), pu.t_end - T, T, s.grid)
-        oc = o["classified"]
-        act = sc["active"].cpu().numpy()
-        np.testing.assert_array_equal(act, oc["active"])
-        lsf = sc["log_sf"].cpu().numpy()
-        np.testing.assert_allclose(lsf, oc["log_sf"], atol=1e-4)
-        ok = np.abs(oc["log_sf"] - np.log(0.89)) > SF_MARGIN
-        ok &= ~((oc["log_sf"] <= np.log(0.89)) & (np.abs(oc["snr"] / 1.5 - 1.0) <= SNR_MARGIN))
+        prm = dict(tau_sf=0.89, tau_comb=1.5, M=4, d=3, h_min=4)
+        b = oracle.bin_events(s.W, s.H, x, y, t, p, pu.t_end - T, T)
+        act = sc["active"].cpu().numpy().astype(np.int64)
+        np.testing.assert_array_equal(act, np.flatnonzero(b["counts"] >= 6))
+        P32 = c.slide_spectra()[1].cpu().numpy()  # |F|^2 of the state the comb scored
+        rot, close = oracle_margins.decisions(b, act, P32, s.grid, prm)
+        assert close.mean() < 0.01
         gm = mask.cpu().numpy()
-        np.testing.assert_array_equal(gm[act[ok]], oc["mask"][act[ok]])
-        if ok.all():
-            n = int(nb.item())
-            np.testing.assert_array_equal(bx[:n].cpu().numpy(), o["boxes"])
-        assert gm[s.drones[0]["keys"]].mean() > 0.3
+        np.testing.assert_array_equal(gm[act[~close]], rot[~close].astype(np.uint8))
+        n = int(nb.item())
+        np.testing.assert_array_equal(bx[:n].cpu().numpy(),
+                                      oracle_margins.segment(gm, s.W, s.H, 147, 19.05, cap=256))
+        if not close.any():
+            om = np.zeros(s.W * s.H, np.uint8)
+            om[act[rot]] = 1
+            np.testing.assert_array_equal(
+                bx[:n].cpu().numpy(), oracle_margins.segment(om, s.W, s.H, 147, 19.05, cap=256))
     c.stats()
     c.close()
 
