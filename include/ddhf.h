@@ -336,6 +336,13 @@ ddhf_status ddhf_export_scores(ddhf_ctx *ctx, int32_t slot, uint32_t *active, fl
                                float *snr, int32_t *f0_bin, int64_t *counts,
                                ddhf_stream stream);
 
+/* The 8-connected labels (as ddhf_label writes them) of slot w's rotor mask
+ * from the last ddhf_detect / ddhf_detect_batch (Sec. 3.5 "Segmentation mask
+ * processing"): labels[W*H] (device int32), a copy of what the detection
+ * computed, so that a caller that needs them (row bands) does not label the
+ * mask again. */
+ddhf_status ddhf_export_labels(ddhf_ctx *ctx, int32_t slot, int32_t *labels, ddhf_stream stream);
+
 /* Tracing: when enable is nonzero, CUDA events bracket the stages of every
  * later ddhf_detect / ddhf_detect_batch call (also inside a captured graph,
  * as external event nodes; enabling or disabling drops a cached graph).

@@ -75,7 +75,7 @@ class BandDetector:
         [2, W], comps [k, 6])."""
         ddhf.ddhf_detect(self.ctx.h, x, y, t, p, x.numel(), t0, window_us, self.bx,
                          self.bx.shape[0], self.nbx, self.mask)
-        ddhf.ddhf_label(self.ctx.h, self.mask, self.labels)
+        ddhf.ddhf_export_labels(self.ctx.h, 0, self.labels)  # the detection's own labels
         ddhf.ddhf_components(self.ctx.h, self.labels, self.row0, self.comps, self.comp_cap,
                              self.ncomp)
         lab = self.labels.view(self.h, self.W)

@@ -850,6 +850,18 @@ ddhf_status ddhf_export_scores(ddhf_ctx *h, int32_t slot, uint32_t *active, floa
   return DDHF_OK;
 }
 
+ddhf_status ddhf_export_labels(ddhf_ctx *h, int32_t slot, int32_t *labels, ddhf_stream stream) {
+  if (!h) return DDHF_ERR_INVALID_ARG;
+  Ctx *c = &h->c;
+  if (slot < 0 || slot >= c->max_windows || !labels)
+    return fail(c, DDHF_ERR_INVALID_ARG, "bad label export arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  DDHF_CUDA_TRY(c, cudaMemcpyAsync(labels, c->slots[slot].labels, c->npx * sizeof(int32_t),
+                                   cudaMemcpyDeviceToDevice, s));
+  return DDHF_OK;
+}
+
 ddhf_status ddhf_get_stats(ddhf_ctx *h, ddhf_stats *out) {
   if (!h || !out) return DDHF_ERR_INVALID_ARG;
   Ctx *c = &h->c;

@@ -218,7 +218,8 @@ __device__ __forceinline__ uint64_t mod_barrett(uint64_t x, uint64_t D, uint64_t
 // sin(pi x) and cos(pi x) for |x| <= 1: x = y + q/2 with q = rint(2x) (the
 // subtraction is exact), then sin(pi y) = y P(y^2) and cos(pi y) = 1 + y^2 C(y^2)
 // on |y| <= 1/4 with polynomials fitted by weighted least squares (relative
-// error, FP64) and rounded to FP32; the quadrant q mod 4 swaps and negates.
+// error, FP64) and rounded to FP32 (paper_2603_08386_gb300/fit_sincospi.py
+// regenerates them); the quadrant q mod 4 swaps and negates.
 // Error within 2 ulp of the exact values (checked against sincospif).
 __device__ __forceinline__ void sincospi_reduced(float x, float &s, float &c) {
   const float q = rintf(__fmul_rn(2.f, x));

@@ -134,6 +134,7 @@ SIGNATURES = {
     "ddhf_slide_detect": (_I32, [_VP, _VP, _I32, _VP, _VP, _VP]),
     "ddhf_slide_get_stats": (_I32, [_VP, ctypes.POINTER(ddhf_slide_stats)]),
     "ddhf_measure_pipes": (_I32, [ctypes.POINTER(ddhf_pipe_peaks), _I32, _VP]),
+    "ddhf_export_labels": (_I32, [_VP, _I32, _VP, _VP]),
 }
 
 _lib = None
@@ -348,6 +349,10 @@ def ddhf_detect_batch(ctx, windows, boxes, cap, n_boxes, masks_out=None, use_gra
 def ddhf_export_scores(ctx, slot, active, log_sf, snr, f0_bin, counts, stream=None):
     _check(load().ddhf_export_scores(ctx, int(slot), _ptr(active), _ptr(log_sf), _ptr(snr),
                                      _ptr(f0_bin), _ptr(counts), _stream(stream)), ctx)
+
+
+def ddhf_export_labels(ctx, slot, labels, stream=None):
+    _check(load().ddhf_export_labels(ctx, int(slot), _ptr(labels), _stream(stream)), ctx)
 
 
 def ddhf_enable_stage_timing(ctx, enable=True):
