@@ -218,6 +218,14 @@ ddhf_status ddhf_hybrid_geometry(const ddhf_grid *grid, int64_t window_us, int32
                                  int64_t *s_us, int32_t *rows, int32_t *threshold,
                                  float *dec);
 
+/* Test hook, not in the paper: the device allocations that ddhf_create makes
+ * (its workspace) succeed n more times, then the next one fails as if the
+ * device were out of memory (without calling cudaMalloc), and the hook
+ * disarms; n = -1 disarms it. ddhf_create then returns DDHF_ERR_CUDA with
+ * every allocation it made released. Process-wide; not for concurrent use
+ * with other contexts being created. */
+ddhf_status ddhf_debug_fail_alloc_after(int32_t n);
+
 /* Table 2 final values. out: host pointer. */
 ddhf_status ddhf_default_params(ddhf_params *out);
 

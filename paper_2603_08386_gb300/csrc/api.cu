@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <new>
 
 #include "ddhf_internal.cuh"
@@ -26,9 +27,20 @@ __global__ void k_copy_counts(int64_t *dst, const uint64_t *counters) {
   if (threadIdx.x < 4) dst[threadIdx.x] = (int64_t)counters[threadIdx.x];
 }
 
+// Injected allocation failure (ddhf_debug_fail_alloc_after): while armed, the
+// countdown reaches 0 at the allocation that fails.
+std::atomic<int> g_fail_alloc_countdown{-1};
+
 template <typename T>
 ddhf_status dev_alloc(Ctx *c, T **p, size_t count) {
   void *q = nullptr;
+  int left = g_fail_alloc_countdown.load();
+  while (left >= 0 && !g_fail_alloc_countdown.compare_exchange_weak(left, left - 1)) {
+  }
+  if (left == 0) {
+    c->last_error = "cudaMalloc: out of memory (injected failure)";
+    return DDHF_ERR_CUDA;
+  }
   cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
   if (e != cudaSuccess) {
     c->last_error = std::string("cudaMalloc: ") + cudaGetErrorString(e);
@@ -212,11 +224,15 @@ ddhf_status run_detect(Ctx *c, const ddhf_window *wins, int nw, ddhf_box *boxes,
     DDHF_CUDA_TRY(c, cudaMemsetAsync(c->qctl, 0, sizeof(uint32_t), s));  // heavy count
     for (int w = 0; w < nw; ++w) {
       const ddhf_window &W = wins[w];
+      NvtxRange r("ddhf binning");
       DDHF_CUDA_TRY(c, cudaMemsetAsync(c->slots[w].mask, 0, c->npx, s));
       DDHF_TRY(bin_into(c, w, W.x, W.y, W.t_us, W.p, W.n, W.t0_us, W.window_us, s));
     }
     if (c->timing) DDHF_CUDA_TRY(c, record_stage(c, 1, s));
-    DDHF_TRY(launch_fused(c, nw, true, nullptr, 0, s));
+    {
+      NvtxRange r("ddhf spectra + comb (fused)");
+      DDHF_TRY(launch_fused(c, nw, true, nullptr, 0, s));
+    }
   } else if (c->tuning.overlap && c->pbuf2 && nw > 1) {
     // per window as below, but the comb kernel of window w runs on the aux
     // stream while the main stream bins window w + 1 and computes its spectra
@@ -230,17 +246,27 @@ ddhf_status run_detect(Ctx *c, const ddhf_window *wins, int nw, ddhf_box *boxes,
       float *buf = (w & 1) ? c->pbuf2 : c->pbuf;
       cudaEvent_t *we = c->timing ? &c->win_ev[5 * w] : nullptr;
       if (we) DDHF_CUDA_TRY(c, record_event(we[0], s));
-      DDHF_CUDA_TRY(c, cudaMemsetAsync(c->qctl, 0, sizeof(uint32_t), s));
-      DDHF_TRY(bin_into(c, w, W.x, W.y, W.t_us, W.p, W.n, W.t0_us, W.window_us, s));
+      {
+        NvtxRange r("ddhf binning");
+        DDHF_CUDA_TRY(c, cudaMemsetAsync(c->qctl, 0, sizeof(uint32_t), s));
+        DDHF_TRY(bin_into(c, w, W.x, W.y, W.t_us, W.p, W.n, W.t0_us, W.window_us, s));
+      }
       if (we) DDHF_CUDA_TRY(c, record_event(we[1], s));
       if (w >= 2) DDHF_CUDA_TRY(c, cudaStreamWaitEvent(s, c->ov_comb[w & 1], 0));
-      DDHF_TRY(launch_spectrum_slot(c, w, buf, c->npx, s, c->pbuf_ld));
+      {
+        NvtxRange r("ddhf spectra");
+        DDHF_TRY(launch_spectrum_slot(c, w, buf, c->npx, s, c->pbuf_ld));
+      }
       if (we) DDHF_CUDA_TRY(c, record_event(we[2], s));
       DDHF_CUDA_TRY(c, cudaEventRecord(c->ov_spec[w & 1], s));
       DDHF_CUDA_TRY(c, cudaStreamWaitEvent(b, c->ov_spec[w & 1], 0));
       Slot &sl = c->slots[w];
       if (we) DDHF_CUDA_TRY(c, record_event(we[3], b));
-      DDHF_TRY(launch_comb(c, buf, c->npx, sl.log_sf, sl.snr, sl.f0, sl.mask, b, w, c->pbuf_ld));
+      {
+        NvtxRange r("ddhf comb");
+        DDHF_TRY(launch_comb(c, buf, c->npx, sl.log_sf, sl.snr, sl.f0, sl.mask, b, w,
+                             c->pbuf_ld));
+      }
       if (we) DDHF_CUDA_TRY(c, record_event(we[4], b));
       DDHF_CUDA_TRY(c, cudaEventRecord(c->ov_comb[w & 1], b));
     }
@@ -252,15 +278,24 @@ ddhf_status run_detect(Ctx *c, const ddhf_window *wins, int nw, ddhf_box *boxes,
       const ddhf_window &W = wins[w];
       cudaEvent_t *we = c->timing ? &c->win_ev[5 * w] : nullptr;
       if (we) DDHF_CUDA_TRY(c, record_event(we[0], s));
-      DDHF_CUDA_TRY(c, cudaMemsetAsync(c->qctl, 0, sizeof(uint32_t), s));
-      DDHF_TRY(bin_into(c, w, W.x, W.y, W.t_us, W.p, W.n, W.t0_us, W.window_us, s));
+      {
+        NvtxRange r("ddhf binning");
+        DDHF_CUDA_TRY(c, cudaMemsetAsync(c->qctl, 0, sizeof(uint32_t), s));
+        DDHF_TRY(bin_into(c, w, W.x, W.y, W.t_us, W.p, W.n, W.t0_us, W.window_us, s));
+      }
       if (we) DDHF_CUDA_TRY(c, record_event(we[1], s));
       Slot &sl = c->slots[w];
-      DDHF_TRY(launch_spectrum_slot(c, w, c->pbuf, c->npx, s, c->pbuf_ld));
+      {
+        NvtxRange r("ddhf spectra");
+        DDHF_TRY(launch_spectrum_slot(c, w, c->pbuf, c->npx, s, c->pbuf_ld));
+      }
       if (we) DDHF_CUDA_TRY(c, record_event(we[2], s));
       if (we) DDHF_CUDA_TRY(c, record_event(we[3], s));
-      DDHF_TRY(launch_comb(c, c->pbuf, c->npx, sl.log_sf, sl.snr, sl.f0, sl.mask, s, w,
-                           c->pbuf_ld));
+      {
+        NvtxRange r("ddhf comb");
+        DDHF_TRY(launch_comb(c, c->pbuf, c->npx, sl.log_sf, sl.snr, sl.f0, sl.mask, s, w,
+                             c->pbuf_ld));
+      }
       if (we) DDHF_CUDA_TRY(c, record_event(we[4], s));
     }
   }
@@ -269,6 +304,7 @@ ddhf_status run_detect(Ctx *c, const ddhf_window *wins, int nw, ddhf_box *boxes,
   if (c->timing) DDHF_CUDA_TRY(c, record_stage(c, 2, s));
   for (int w = 0; w < nw; ++w) {
     Slot &sl = c->slots[w];
+    NvtxRange r("ddhf labels + boxes");
     DDHF_TRY(launch_label(c, sl.mask, sl.labels, sl.counters + 7, s));
     DDHF_TRY(launch_boxes(c, sl.labels, boxes + (int64_t)w * cap, cap, sl.nbox, s));
     DDHF_CUDA_TRY(c, cudaMemcpyAsync(n_boxes_dev + w, sl.nbox, sizeof(int32_t),
@@ -302,6 +338,12 @@ const char *ddhf_status_string(ddhf_status s) {
     case DDHF_ERR_STATE: return "call out of order";
   }
   return "unknown status";
+}
+
+ddhf_status ddhf_debug_fail_alloc_after(int32_t n) {
+  if (n < -1) return DDHF_ERR_INVALID_ARG;
+  g_fail_alloc_countdown.store(n);
+  return DDHF_OK;
 }
 
 ddhf_status ddhf_default_params(ddhf_params *out) {

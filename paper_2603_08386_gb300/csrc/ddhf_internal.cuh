@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 #include <stdio.h>
 
@@ -194,6 +195,15 @@ struct Ctx {
 };
 
 // ---------------------------------------------------------------- helpers
+
+// An NVTX range (shown by profilers on the host timeline) around the launches
+// of one stage; free when no profiler is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 #define DDHF_CUDA_TRY(ctx, call)                                                   \
   do {                                                                             \

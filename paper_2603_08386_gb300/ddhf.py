@@ -135,6 +135,7 @@ SIGNATURES = {
     "ddhf_slide_get_stats": (_I32, [_VP, ctypes.POINTER(ddhf_slide_stats)]),
     "ddhf_measure_pipes": (_I32, [ctypes.POINTER(ddhf_pipe_peaks), _I32, _VP]),
     "ddhf_export_labels": (_I32, [_VP, _I32, _VP, _VP]),
+    "ddhf_debug_fail_alloc_after": (_I32, [_I32]),
 }
 
 _lib = None
@@ -349,6 +350,10 @@ def ddhf_detect_batch(ctx, windows, boxes, cap, n_boxes, masks_out=None, use_gra
 def ddhf_export_scores(ctx, slot, active, log_sf, snr, f0_bin, counts, stream=None):
     _check(load().ddhf_export_scores(ctx, int(slot), _ptr(active), _ptr(log_sf), _ptr(snr),
                                      _ptr(f0_bin), _ptr(counts), _stream(stream)), ctx)
+
+
+def ddhf_debug_fail_alloc_after(n):
+    _check(load().ddhf_debug_fail_alloc_after(int(n)))
 
 
 def ddhf_export_labels(ctx, slot, labels, stream=None):

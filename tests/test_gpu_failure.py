@@ -69,3 +69,39 @@ def test_loop_limit_runs_out_and_context_recovers():
     with pytest.raises(ddhf.DDHFError):
         ddhf.ddhf_set_loop_limit(c.h, 0)
     c.close()
+
+
+def test_injected_allocation_failure_releases_everything():
+    # every allocation of ddhf_create fails in turn (a host-side injected
+    # failure, no device fault): the call returns DDHF_ERR_CUDA, frees what it
+    # had allocated, and a context made afterwards works
+    s = synth.small_scene(9, W=40, H=30, n_noise=5_000)
+    g = ddhf.make_grid(*s.grid)
+    prm = ddhf.default_params()
+    x, y, t, p = ddhf.events_to_device(s)
+    warm = ddhf.Context(s.W, s.H, s.grid, max_events=s.n)  # loads the library's code first
+    warm.detect(x, y, t, p, s.t0, s.window_us)
+    warm.stats()
+    warm.close()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    failed = 0
+    for n in range(0, 40, 3):
+        ddhf.ddhf_debug_fail_alloc_after(n)
+        try:
+            h = ddhf.ddhf_create(s.W, s.H, g, prm, s.n, 2)
+        except ddhf.DDHFError as e:
+            assert e.status == 2
+            failed += 1
+            continue
+        finally:
+            ddhf.ddhf_debug_fail_alloc_after(-1)
+        ddhf.ddhf_destroy(h)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert failed >= 5
+    assert abs(free1 - free0) <= (2 << 20), (free0, free1)  # nothing leaked (2 MiB slack)
+    c = ddhf.Context(s.W, s.H, s.grid, max_events=s.n)
+    c.detect(x, y, t, p, s.t0, s.window_us)
+    c.stats()
+    c.close()
