@@ -54,12 +54,10 @@ WORKLOAD = ("C3: {W}x{H}, 8 consecutive 30 ms windows x 4 streams per step, Pare
             "Table 2 parameters")
 OPS_PER_TERM = 3  # FP32 FMA-pipe lane-ops per term of the blocked three-multiplication form
 # DRAM bytes (read + write) per active pixel of one launch, from one ncu capture
-# of a kernel on a 640x360 window of the same recipe, scaled to a launch by its
-# active pixels (the traffic is per-pixel rows). A figure is listed only while
-# the kernel is the one that was captured: the spectrum kernel (2867 B) and
-# the comb kernel (3043 B) have both changed since their captures, so the
-# bench reports their traffic as null.
-TRAFFIC_PER_PIXEL = {}
+# of the kernel on a 640x360 window of the same recipe (profiles/), scaled to a
+# launch by its active pixels (the traffic is per-pixel rows). A figure is
+# listed only while the kernel is the one that was captured.
+TRAFFIC_PER_PIXEL = {"k_comb<2>": 3036.0}
 TRAFFIC_NOTE = ("null: the ncu DRAM capture of this kernel predates its current code "
                 "(profiles/ keeps the earlier figure)")
 
@@ -775,6 +773,7 @@ def main():
                      ops="3 FP32 FMA-pipe lane-ops per term (three-multiplication complex "
                          "product)")
     roof_comb = None
+    comb_reg = 512 < nb <= 768  # Table 2's M = 4, d = 3 on this grid: the register form
     if not fused_mode:
         pk = measured_peaks()
         # algorithmic bytes: read every active pixel's spectrum row, write its
@@ -784,12 +783,14 @@ def main():
         ach = comb_bytes / (comb_t * 1e-3) / 1e9
         roof_comb = dict(bound="hbm", achieved=ach, peak=pk["hbm_gbs"], unit="GB/s",
                          frac=ach / pk["hbm_gbs"],
-                         traffic=TRAFFIC_PER_PIXEL["k_comb<0>"] * n_act / nwin
-                         if ("k_comb<0>" in TRAFFIC_PER_PIXEL and nb <= 1024) else None,
+                         traffic=TRAFFIC_PER_PIXEL["k_comb<2>"] * n_act / nwin
+                         if ("k_comb<2>" in TRAFFIC_PER_PIXEL and comb_reg) else None,
                          traffic_unit="B per launch (window)",
-                         traffic_note=None if ("k_comb<0>" in TRAFFIC_PER_PIXEL and nb <= 1024)
+                         traffic_note=None if ("k_comb<2>" in TRAFFIC_PER_PIXEL and comb_reg)
                          else TRAFFIC_NOTE,
-                         kernel="SF + comb kernel (k_comb<0>)", launches_per_step=nwin,
+                         kernel="SF + comb kernel (k_comb<2>: register form, 24 bins per lane)"
+                         if comb_reg else "SF + comb kernel (k_comb<3>: shared-memory form)",
+                         launches_per_step=nwin,
                          launch_ms=comb_t / nwin, bytes_per_launch=comb_bytes / nwin,
                          kernel_ms_per_step=comb_t,
                          share_of_step=comb_t / ms_step, peak_source=pk["source"],

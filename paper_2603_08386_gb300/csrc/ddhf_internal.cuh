@@ -253,9 +253,11 @@ __device__ __forceinline__ void sincospi_reduced(float x, float &s, float &c) {
 }
 
 // e^{-2 pi i r / D} for an exact residue 0 <= r < D, via sin/cos(pi x) of the
-// half-open turn x = 2r/D folded to [-1, 1].
+// half-open turn x = 2r/D folded to [-1, 1]. D < 2^31, so r converts from 32
+// bits (the same rounding as from 64 bits, without a 64-bit conversion, which
+// runs on the FP64 pipe).
 __device__ __forceinline__ float2 phasor_of_residue(uint64_t r, float two_over_denom) {
-  float x = __fmul_rn((float)r, two_over_denom);
+  float x = __fmul_rn((float)(uint32_t)r, two_over_denom);
   if (x > 1.0f) x = __fsub_rn(x, 2.0f);
   float s, c;
   sincospi_reduced(x, s, c);

@@ -98,8 +98,8 @@ __global__ void __launch_bounds__(256) k_softcomb(SoftArgs A) {
           const uint64_t tau = wv & 0x7fffffffu;
           const float sg = (wv & kSignBit) ? -1.f : 1.f;
           const uint64_t r = mod_barrett(ai * tau, D9, A.barrett);
-          float x = __fmul_rn((float)r, 1e-9f);
-          x = __fadd_rn(x, __fmul_rn(__fmul_rn(fr, (float)tau), 1e-6f));
+          float x = __fmul_rn((float)(uint32_t)r, 1e-9f);  // r < 1e9, tau < 2^31: 32-bit
+          x = __fadd_rn(x, __fmul_rn(__fmul_rn(fr, (float)(uint32_t)tau), 1e-6f));
           x = __fsub_rn(x, cff);
           x = __fsub_rn(x, rintf(x));                                 // [-0.5, 0.5] cycles
           float sn, cs;
