@@ -165,6 +165,7 @@ void derive_constants(Ctx *c) {
   cc.lo_r = lo;
   cc.bw = hi - lo + 1;
   cc.ln_tau_sf = (float)log((double)p.tau_sf);
+  cc.inv_N = (float)(1.0 / (double)N);
   cc.tau_comb = p.tau_comb;
 }
 

@@ -469,7 +469,7 @@ __device__ __forceinline__ CombOut comb_warp_generic(const float *Pw, const Comb
 // instructions per pixel:
 //  * the log sum of Eq. 7 (base 2, scaled by ln 2 once) shares its pass with
 //    a histogram of 768 buckets linear in P over [0, 1.5 mean) (values above
-//    go to the last; two 16-bit counters per word);
+//    go to the last);
 //  * the buckets holding ranks lo_r and hi_r bound the candidate bins; at
 //    most 64 candidates (about 31 on C3's spectra) are compacted into shared
 //    memory and sorted in registers as 32-bit keys (value bits relative to
@@ -495,19 +495,19 @@ __device__ __forceinline__ CombOut comb_warp_generic(const float *Pw, const Comb
 // Pixels whose candidates do not fit (more than 64, or a value range above
 // 2^22 ulps) take an exact radix selection of the band instead.
 // Scratch (bytes from the scratch base, 16-byte aligned):
-//   [0, 1536)   histogram u32[384]; once the band's buckets are located, over
+//   [0, 3072)   histogram u32[768]; once the band's buckets are located, over
 //               it: candidate value bits u32[64] at 0 and their bins u16[64]
 //               at 256; once the band is in registers: N(w) of candidate
 //               w_lo + i, f32[n_cand] (-1: complement empty), when it fits
-//   [1536, +16 ceil(N/4))  window maxima f32[N]
+//   [3072, +16 ceil(N/4))  window maxima f32[N]
 //   then N(w), when it does not fit over the histogram
 struct CombFast {
   static constexpr int kBuckets = 768;
   static constexpr int kHist = 0;
-  static constexpr int kHistBytes = 1536;
+  static constexpr int kHistBytes = 3072;
   static constexpr int kCandV = 0;
   static constexpr int kCandJ = 256;
-  static constexpr int kRec = 1536;
+  static constexpr int kRec = 3072;
   __host__ __device__ static int rec_end(int N) { return kRec + ((4 * N + 15) & ~15); }
   __host__ __device__ static int nw_off(int N, int n_cand) {
     return 4 * n_cand <= kHistBytes ? 0 : rec_end(N);
@@ -527,8 +527,11 @@ struct CombReg {
   static constexpr int kBPL = 24;
   static constexpr int kM = 4;
   static constexpr int kD = 3;
+  // every candidate then has all M windows and a non-empty complement
   __host__ __device__ static bool fits(const CombConst &cc) {
-    return cc.N > 16 * kBPL && cc.N <= 32 * kBPL && cc.M == kM && cc.d == kD;
+    return cc.N > 16 * kBPL && cc.N <= 32 * kBPL && cc.M == kM && cc.d == kD &&
+           kM * cc.w_hi <= cc.N - 1 - kD && cc.N > kM * (2 * kD + 1) &&
+           cc.w_hi - cc.w_lo + 1 <= 256;
   }
 };
 
@@ -666,13 +669,11 @@ __device__ __forceinline__ int bucket_of(float v, float scale) {
   return (int)(bucket_bits(v, scale) & 1023u);
 }
 
-// Add one to the bucket whose bucket_bits are ybits in the packed histogram
-// (two 16-bit counters per word) at shared address hist_sa: word g >> 1, the
-// high half for odd g.
+// Add one to the bucket whose bucket_bits are ybits in the histogram at
+// shared address hist_sa (one counter per bucket).
 __device__ __forceinline__ void hist_add(uint32_t hist_sa, uint32_t ybits) {
-  const uint32_t a = hist_sa + ((ybits & 1022u) << 1);
-  const uint32_t inc = (ybits & 1u) * 0xFFFFu + 1u;
-  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"(inc) : "memory");
+  const uint32_t a = hist_sa + ((ybits & 1023u) << 2);
+  asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(a) : "memory");
 }
 
 // M_valid(w) = #{m <= M : m w + d <= N - 1}, the in-band harmonics (a prefix).
@@ -703,10 +704,8 @@ __device__ __forceinline__ float comb_cand_nw(const float *rec, int w, const Com
   return comb_nw(s, mv);
 }
 
-// The buckets holding full ranks lo_r and hi_r in the packed histogram; lane
-// l owns buckets [24 l, 24 l + 24) (words [12 l, 12 l + 12)); the two 16-bit
-// halves never carry into each other (a bucket holds at most N <= 1024 bins,
-// 12 words at most 12288). Returns the first and last candidate bucket, the
+// The buckets holding full ranks lo_r and hi_r in the histogram; lane l owns
+// buckets [24 l, 24 l + 24). Returns the first and last candidate bucket, the
 // bins below the first (cb) and the candidate count.
 struct BandBuckets {
   int g0, g1, cb, ncand;
@@ -716,14 +715,14 @@ __device__ __forceinline__ BandBuckets comb_locate(const uint32_t *hist, int N, 
   const int lane = threadIdx.x & 31;
   uint32_t lsum;
   {
-    const uint4 *h4 = reinterpret_cast<const uint4 *>(hist) + lane * 3;  // no bank conflicts
+    const uint4 *h4 = reinterpret_cast<const uint4 *>(hist) + lane * 6;
     uint32_t s2 = 0;
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const uint4 t = h4[q];
+    for (int q = 0; q < 6; ++q) {
+      const uint4 t = h4[(q + (lane >> 2)) % 6];  // rotated: no bank conflicts
       s2 += t.x + t.y + t.z + t.w;
     }
-    lsum = (s2 & 0xFFFFu) + (s2 >> 16);
+    lsum = s2;
   }
   uint32_t tot;
   const uint32_t lex = warp_excl_scan<uint32_t>(lsum, tot);
@@ -739,8 +738,7 @@ __device__ __forceinline__ BandBuckets comb_locate(const uint32_t *hist, int N, 
       bad = true;
     }
     const uint32_t base = __shfl_sync(0xffffffffu, lex, src);
-    const uint32_t wv = lane < 24 ? hist[src * 12 + (lane >> 1)] : 0u;
-    const uint32_t h = (lane & 1) ? (wv >> 16) : (wv & 0xFFFFu);
+    const uint32_t h = lane < 24 ? hist[src * 24 + lane] : 0u;
     uint32_t t2;
     const uint32_t ex = warp_excl_scan<uint32_t>(h, t2) + base;
     int s2 = __ffs(__ballot_sync(0xffffffffu, R >= ex && R < ex + h)) - 1;
@@ -794,6 +792,8 @@ __device__ __forceinline__ bool comb_band_sorted(const unsigned char *scratch, i
 
 // N(w) of every candidate into nws[], the largest and its candidate index
 // (the first of equal maxima; -1 / INT_MAX when every complement is empty).
+// KM, KD > 0 (the register form): the comb's M and d, with every candidate
+// known to have all M windows and a non-empty complement (CombReg::fits).
 template <int KM, int KD>
 __device__ __forceinline__ void comb_nw_all(const float *rec, float *nws, const CombConst &cc,
                                             bool uniform, float &maxnw, int &maxi) {
@@ -801,12 +801,34 @@ __device__ __forceinline__ void comb_nw_all(const float *rec, float *nws, const 
   const int n_cand = cc.w_hi - cc.w_lo + 1;
   maxnw = -1.f;
   maxi = 0x7fffffff;
-  for (int i = lane; i < n_cand; i += 32) {
-    const float nw = comb_cand_nw<KM, KD>(rec, cc.w_lo + i, cc, uniform);
-    nws[i] = nw;
-    if (nw > maxnw) {
-      maxnw = nw;
-      maxi = i;
+  if (KM) {
+    // every candidate has all KM windows and a non-empty complement: N(w) is
+    // a plain sum of KM window maxima
+#pragma unroll 1
+    for (int k = 0; k < 8; ++k) {
+      const int i = lane + 32 * k;
+      if (32 * k >= n_cand) break;
+      if (i < n_cand) {
+        const int w = cc.w_lo + i;
+        float sm = rec[w];
+#pragma unroll
+        for (int m = 2; m <= KM; ++m) sm = __fadd_rn(sm, rec[m * w]);
+        const float nw = comb_nw(sm, KM);
+        nws[i] = nw;
+        if (nw > maxnw) {
+          maxnw = nw;
+          maxi = i;
+        }
+      }
+    }
+  } else {
+    for (int i = lane; i < n_cand; i += 32) {
+      const float nw = comb_cand_nw<0, 0>(rec, cc.w_lo + i, cc, uniform);
+      nws[i] = nw;
+      if (nw > maxnw) {
+        maxnw = nw;
+        maxi = i;
+      }
     }
   }
 #pragma unroll
@@ -842,7 +864,7 @@ __device__ __forceinline__ void comb_best(const float *Pw, const float *nws, con
   const bool band_lane = lane < bw;
   // SNR of candidate w with N(w) = nw
   auto eval = [&](int w, float nw) -> float {
-    const int mv = uniform ? M : comb_mvalid(w, M, N - 1 - d);
+    const int mv = (KM || uniform) ? M : comb_mvalid(w, M, N - 1 - d);
     const bool disjoint = w >= span;
     const int h = disjoint ? mv * span : (mv - 1) * w + span;
     const int c = N - h;
@@ -852,7 +874,7 @@ __device__ __forceinline__ void comb_best(const float *Pw, const float *nws, con
     const int below = __popc(__ballot_sync(0xffffffffu, blw));
     // band positions inside H(w)
     bool rm = false;
-    if (KM && uniform) {
+    if (KM) {
 #pragma unroll
       for (int m = 1; m <= KM; ++m) rm |= (uint32_t)(bj - m * w + d) <= (uint32_t)(2 * d);
     } else {
@@ -1143,8 +1165,9 @@ __device__ __forceinline__ CombOut comb_warp_fast_regs(const float *Pw, const Co
   for (int i = 0; i < kB; ++i) sum = __fadd_rn(sum, v[i]);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) sum = __fadd_rn(sum, __shfl_xor_sync(0xffffffffu, sum, o));
-  const float fN = (float)N;
-  const float scale = __fdiv_rn(512.f, __fdiv_rn(sum, fN));
+  // 512 / mean; any positive scale gives exact buckets (the histogram and the
+  // candidate test use the same one), so an approximate reciprocal will do
+  const float scale = __fmul_rn(512.f * (float)N, rcp_approx(sum));
   __syncwarp();
   float sl2 = 0.f;
 #pragma unroll
@@ -1160,7 +1183,8 @@ __device__ __forceinline__ CombOut comb_warp_fast_regs(const float *Pw, const Co
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) sl2 = __fadd_rn(sl2, __shfl_xor_sync(0xffffffffu, sl2, o));
   const float slog = __fmul_rn(sl2, 0.693147180559945309f);
-  out.log_sf = sum > 0.f ? __fsub_rn(__fdiv_rn(slog, fN), __logf(__fdiv_rn(sum, fN))) : 0.f;
+  out.log_sf = sum > 0.f ? __fsub_rn(__fmul_rn(slog, cc.inv_N), __logf(__fmul_rn(sum, cc.inv_N)))
+                         : 0.f;
   if (!(out.log_sf <= cc.ln_tau_sf) || cc.w_hi < cc.w_lo) return out;
   __syncwarp();
 

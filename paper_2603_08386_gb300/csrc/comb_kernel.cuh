@@ -13,9 +13,10 @@ namespace ddhf {
 
 // The row is copied to shared memory with all of a lane's loads in flight at
 // once (16-byte loads when the rows are 16-byte aligned), then scored by
-// comb_warp; with spec_smem = 0 (the generic comb on a spectrum too large for
-// shared memory, real input only) comb_warp reads the row in global memory
-// and shared memory holds its scratch alone. 4 warps per block; the register form of the fast variant is held
+// comb_warp; with spec_smem = 0 (real input only: the register form on
+// 16-byte aligned rows, or the generic comb on a spectrum too large for
+// shared memory) comb_warp reads the row in global memory and shared memory
+// holds its scratch alone. 4 warps per block; the register form of the fast variant is held
 // to 80 registers (6 blocks, 24 warps per SM; its 7.4 KB of shared memory per
 // warp at 750 bins would allow 7), the shared-memory form to 64.
 template <int NW, bool CPLX>
@@ -128,8 +129,13 @@ ddhf_status launch_comb_t(Ctx *c, const float *P, int64_t cap_px, float *log_sf,
   const int scratch_b = (comb_scratch_bytes(c->comb, variant) + 15) & ~15;
   const int spec_b = (c->grid.n_bins * 4 + 15) & ~15;
   int wpb = 4, spec_smem = 1;
-  while (wpb > 1 && (spec_b + scratch_b) * wpb > max_smem) wpb >>= 1;
-  if ((spec_b + scratch_b) * wpb > max_smem) {
+  // the register form reads its rows where they are when they are 16-byte
+  // aligned (each lane loads its 96 contiguous bytes; the row stays in L1)
+  const int64_t ldv = ld > 0 ? ld : c->grid.n_bins;
+  if (variant == 2 && !CPLX && ldv % 4 == 0 && (reinterpret_cast<uintptr_t>(P) & 15) == 0)
+    spec_smem = 0;
+  while (spec_smem && wpb > 1 && (spec_b + scratch_b) * wpb > max_smem) wpb >>= 1;
+  if (spec_smem && (spec_b + scratch_b) * wpb > max_smem) {
     spec_smem = 0;
     if (CPLX || scratch_b > max_smem) {
       c->last_error = "comb scratch does not fit in shared memory for this grid and comb";

@@ -61,6 +61,7 @@ struct CombConst {
   int32_t bw;       // band width (positions)
   float ln_tau_sf;  // log(tau_sf) in FP32
   float tau_comb;
+  float inv_N;      // 1 / N in FP32
 };
 
 struct GridConst {
