@@ -231,9 +231,13 @@ __device__ __forceinline__ uint64_t mod_barrett(uint64_t x, uint64_t D, uint64_t
 // on |y| <= 1/4 with polynomials fitted by weighted least squares (relative
 // error, FP64) and rounded to FP32 (paper_2603_08386_gb300/fit_sincospi.py
 // regenerates them); the quadrant q mod 4 swaps and negates.
+// q is rounded by adding 1.5 * 2^23 (|2x| <= 2: round to nearest even, as
+// rint does), whose float bits then hold q mod 4 in their lowest bits, so
+// no conversion runs on the special-function pipe.
 // Error within 2 ulp of the exact values (checked against sincospif).
 __device__ __forceinline__ void sincospi_reduced(float x, float &s, float &c) {
-  const float q = rintf(__fmul_rn(2.f, x));
+  const float mq = __fadd_rn(__fmul_rn(2.f, x), 0x1.8p23f);
+  const float q = __fsub_rn(mq, 0x1.8p23f);
   const float y = __fmaf_rn(-0.5f, q, x);
   const float t = __fmul_rn(y, y);
   float p = 0.0810556039f;
@@ -247,7 +251,7 @@ __device__ __forceinline__ void sincospi_reduced(float x, float &s, float &c) {
   k = __fmaf_rn(k, t, 4.05870819f);
   k = __fmaf_rn(k, t, -4.93480206f);
   const float cy = __fmaf_rn(k, t, 1.f);
-  const int iq = (int)q & 3;  // 0: (sy, cy), 1: (cy, -sy), 2: (-sy, -cy), 3: (-cy, sy)
+  const int iq = __float_as_int(mq) & 3;  // 0: (sy, cy), 1: (cy, -sy), 2: (-sy, -cy), 3: (-cy, sy)
   const float s0 = (iq & 1) ? cy : sy, c0 = (iq & 1) ? sy : cy;
   s = (iq & 2) ? -s0 : s0;
   c = (iq == 1 || iq == 2) ? -c0 : c0;

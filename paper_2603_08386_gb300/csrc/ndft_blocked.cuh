@@ -71,17 +71,21 @@ __device__ __forceinline__ void gen_chunk(uint32_t w, bool active, const GridCon
                                           const uint64_t (&arow_mod)[2], float4 *stage) {
   const int lane = threadIdx.x & 31;
   const int e = lane & 15, half = lane >> 4;
-  if (!active) return;
   const uint64_t tau = w & 0x7fffffffu;
-  const uint64_t rz = mod_barrett((half ? g.da16_mod : 0ull) * tau, g.denom, g.barrett);
-  const uint64_t ru = mod_barrett(g.da_mod * tau, g.denom, g.barrett);
+  // the two lanes of an event make one step phasor each (half 0: u, half 1:
+  // v = u^32) and swap them; each makes its own first A row, and half 1 its
+  // first B column u^16 (half 0 starts at u^0 = 1)
+  const uint64_t ra = mod_barrett((half ? g.da32_mod : g.da_mod) * tau, g.denom, g.barrett);
   const uint64_t rs = mod_barrett(arow_mod[half] * tau, g.denom, g.barrett);
-  const uint64_t rv = mod_barrett(g.da32_mod * tau, g.denom, g.barrett);
-  float2 z = phasor_of_residue(rz, g.two_over_denom);
-  const float2 u = phasor_of_residue(ru, g.two_over_denom);
+  const uint64_t rz = mod_barrett(g.da16_mod * tau, g.denom, g.barrett);
+  const float2 pa = phasor_of_residue(ra, g.two_over_denom);
+  const float2 pb = make_float2(__shfl_xor_sync(0xffffffffu, pa.x, 16),
+                                __shfl_xor_sync(0xffffffffu, pa.y, 16));
+  if (!active) return;
+  const float2 u = half ? pb : pa;
+  const float2 v = half ? pa : pb;
   float2 s = phasor_of_residue(rs, g.two_over_denom);
-  const float2 v = phasor_of_residue(rv, g.two_over_denom);
-  if (!half) z = make_float2(1.f, 0.f);
+  float2 z = half ? phasor_of_residue(rz, g.two_over_denom) : make_float2(1.f, 0.f);
   if (w & kSignBit) {
     s.x = -s.x;
     s.y = -s.y;

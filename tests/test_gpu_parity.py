@@ -504,3 +504,44 @@ def test_detect_large_grid():
             s32, w32 = oracle.comb_f32(Ph[a])
             assert w32 == f0[a]
             assert np.float32(s32).view(np.uint32) == np.float32(snr[a]).view(np.uint32)
+
+
+def test_c3_window_full_size_comb_bits():
+    # the benchmarked path on a full 1280x720 C3 window: ddhf_detect with the
+    # bench's tuning (hybrid spectra from 128 events), scores exported, and the
+    # rows it scored (ddhf_power_spectrum HYBRID, the same kernels) given to the
+    # oracle's FP32 comb: SNR bits and dominant bin of ~300 sampled pixels
+    # (the heaviest, random ones, drone pixels) must be equal
+    s = synth.config3_window(stream=2, window=5)
+    c = ctx_for(s, heavy_min=1024, warps_per_block=8, overlap=1, hybrid_min=128)
+    x, y, t, p = ddhf.events_to_device(s)
+    bx, nb, mask = c.detect(x, y, t, p, s.t0, s.window_us, cap=256, want_mask=True)
+    sc = c.scores()
+    P = c.power_spectrum("hybrid")
+    c.stats()
+    c.close()
+    act = sc["active"].cpu().numpy()
+    o = oracle_bin(s)
+    counts = o["counts"][act]
+    rng = np.random.default_rng(11)
+    drone = np.flatnonzero(np.isin(act, np.concatenate([d["keys"] for d in s.drones])))
+    sample = np.unique(np.concatenate([np.argsort(-counts, kind="stable")[:60],
+                                       rng.choice(len(act), 200, replace=False),
+                                       rng.choice(drone, min(60, drone.size), replace=False)]))
+    rows = P[torch.from_numpy(sample).cuda()].cpu().numpy()
+    lsf = sc["log_sf"].cpu().numpy()[sample]
+    snr = sc["snr"].cpu().numpy()[sample]
+    f0 = sc["f0_bin"].cpu().numpy()[sample]
+    ln_tau = np.float32(math.log(0.89))
+    scored = 0
+    for i in range(sample.size):
+        lo = oracle.log_sf(rows[i].astype(np.float64))
+        assert abs(lsf[i] - lo) <= 1e-4 * max(1.0, abs(lo))
+        if abs(lo - math.log(0.89)) > SF_MARGIN:
+            assert (lsf[i] <= ln_tau) == (lo <= math.log(0.89))
+        if lsf[i] <= ln_tau:
+            s32, w32 = oracle.comb_f32(rows[i])
+            assert w32 == f0[i], (sample[i], w32, f0[i])
+            assert np.float32(s32).view(np.uint32) == np.float32(snr[i]).view(np.uint32)
+            scored += 1
+    assert scored > 0.9 * sample.size
