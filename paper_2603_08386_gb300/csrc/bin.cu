@@ -8,7 +8,7 @@
 // scan of that table gives every (digit, chunk) its output offset, and a
 // scatter kernel re-reads its chunk and places each element at
 // offset + (its rank among equal digits earlier in the chunk). The in-chunk
-// rank is computed warp by warp with __match_any_sync and per-warp digit
+// rank is computed warp by warp with one ballot per digit bit and per-warp digit
 // counters in shared memory, so element order inside a digit is input order
 // and every pass is stable; the chunk is staged in shared memory in digit
 // order and written out in contiguous runs; no block waits on another block. The first pass
@@ -62,37 +62,117 @@ __global__ void __launch_bounds__(kBinThreads) k_hist(RawIn raw, const uint32_t 
                                                       uint32_t *__restrict__ hist, int64_t nchunks,
                                                       int shift, int nb) {
   __shared__ uint32_t sh[1 << kMaxDigitBits];
+  constexpr int kU = 8;  // elements per thread with their loads in flight together
   const int64_t n = RAW ? raw.n : (int64_t)*n_dev;
   const int64_t chunk = blockIdx.x;
   const int64_t c0 = chunk * kBinChunk;
   for (int d = threadIdx.x; d < nb; d += blockDim.x) sh[d] = 0;
   __syncthreads();
   const int64_t c1 = min(n, c0 + (int64_t)kBinChunk);
-  for (int64_t base = c0; base < c1; base += blockDim.x) {
-    int64_t e = base + threadIdx.x;
-    uint32_t d = (uint32_t)nb;  // sentinel: not counted
-    if (e < c1) {
-      uint32_t key, val;
-      if (RAW) {
-        if (load_raw(raw, e, key, val)) d = (key >> shift) & (uint32_t)(nb - 1);
-      } else {
-        d = (kin[e] >> shift) & (uint32_t)(nb - 1);
+  for (int64_t base = c0 + threadIdx.x; base < c1; base += (int64_t)kBinThreads * kU) {
+    uint32_t d[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t e = base + (int64_t)u * kBinThreads;
+      d[u] = (uint32_t)nb;  // sentinel: not counted
+      if (e < c1) {
+        if (RAW) {
+          uint32_t key, val;
+          if (load_raw(raw, e, key, val)) d[u] = (key >> shift) & (uint32_t)(nb - 1);
+        } else {
+          d[u] = (kin[e] >> shift) & (uint32_t)(nb - 1);
+        }
       }
     }
-    if (d < (uint32_t)nb) atomicAdd(&sh[d], 1u);
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+      if (d[u] < (uint32_t)nb) atomicAdd(&sh[d[u]], 1u);
   }
   __syncthreads();
   for (int d = threadIdx.x; d < nb; d += blockDim.x) hist[(int64_t)d * nchunks + chunk] = sh[d];
 }
 
-// Exclusive scan in place of a[0..n) (n <= 2048) by one block of kBinThreads
-// threads; returns the total. Uses `tmp` (kBinThreads / 32 words).
-__device__ __forceinline__ uint32_t block_excl_scan(uint32_t *a, int n, uint32_t *tmp) {
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const int per = (n + kBinThreads - 1) / kBinThreads;  // <= 8
-  uint32_t v[8], s = 0;
+// First pass over raw events: the histogram of the first digit per chunk, as
+// k_hist, and each event packed into the (key, value) words the sort carries
+// (key kDropKey for events that are not kept), so that the first scatter reads
+// 8 bytes per event in two coalesced words. VEC: the arrays are aligned for
+// loads of 4 consecutive events (x, y: 8 bytes, t: 2 x 16 bytes, p: 4 bytes).
+template <bool VEC>
+__global__ void __launch_bounds__(kBinThreads) k_hist_pack(RawIn raw, uint32_t *__restrict__ pk,
+                                                           uint32_t *__restrict__ pv,
+                                                           uint32_t *__restrict__ hist,
+                                                           int64_t nchunks, int nb) {
+  __shared__ uint32_t sh[1 << kMaxDigitBits];
+  const int64_t n = raw.n;
+  const int64_t chunk = blockIdx.x;
+  const int64_t c0 = chunk * kBinChunk;
+  for (int d = threadIdx.x; d < nb; d += blockDim.x) sh[d] = 0;
+  __syncthreads();
+  const int64_t c1 = min(n, c0 + (int64_t)kBinChunk);
+  const uint32_t mask = (uint32_t)(nb - 1);
+  // 4 consecutive events per thread and step; 8 steps cover the chunk
+  for (int64_t e0 = c0 + 4 * (int64_t)threadIdx.x; e0 < c1; e0 += 4 * kBinThreads) {
+    uint32_t key[4], val[4];
+    bool kept[4];
+    if (VEC && e0 + 4 <= c1) {
+      const short4 xs = *reinterpret_cast<const short4 *>(raw.x + e0);
+      const short4 ys = *reinterpret_cast<const short4 *>(raw.y + e0);
+      const longlong2 t01 = *reinterpret_cast<const longlong2 *>(raw.t + e0);
+      const longlong2 t23 = *reinterpret_cast<const longlong2 *>(raw.t + e0 + 2);
+      const char4 ps = *reinterpret_cast<const char4 *>(raw.p + e0);
+      const int xx[4] = {xs.x, xs.y, xs.z, xs.w}, yy[4] = {ys.x, ys.y, ys.z, ys.w};
+      const int64_t tt[4] = {t01.x, t01.y, t23.x, t23.y};
+      const int pp[4] = {(int8_t)ps.x, (int8_t)ps.y, (int8_t)ps.z, (int8_t)ps.w};
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
+      for (int u = 0; u < 4; ++u) {
+        const int xv = xx[u], yv = yy[u] - raw.row0;
+        const bool okp = raw.pol01 ? (pp[u] == 0 || pp[u] == 1) : (pp[u] == 1 || pp[u] == -1);
+        const bool neg = raw.pol01 ? (pp[u] == 0) : (pp[u] == -1);
+        const uint64_t dt = (uint64_t)tt[u] - (uint64_t)raw.t0;
+        kept[u] = okp && xv >= 0 && xv < raw.W && yv >= 0 && yv < raw.H && tt[u] >= raw.t0 &&
+                  dt < raw.win;
+        key[u] = (uint32_t)(yv * raw.W + xv);
+        val[u] = (uint32_t)dt | (neg ? kSignBit : 0u);
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        kept[u] = false;
+        key[u] = 0u;
+        val[u] = 0u;
+        if (e0 + u < c1) kept[u] = load_raw(raw, e0 + u, key[u], val[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (!kept[u]) key[u] = kDropKey;
+      else atomicAdd(&sh[key[u] & mask], 1u);
+    }
+    if (VEC && e0 + 4 <= c1) {
+      *reinterpret_cast<uint4 *>(pk + e0) = make_uint4(key[0], key[1], key[2], key[3]);
+      *reinterpret_cast<uint4 *>(pv + e0) = make_uint4(val[0], val[1], val[2], val[3]);
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (e0 + u < c1) {
+          pk[e0 + u] = key[u];
+          pv[e0 + u] = val[u];
+        }
+    }
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < nb; d += blockDim.x) hist[(int64_t)d * nchunks + chunk] = sh[d];
+}
+
+// Exclusive scan in place of a[0..n) (n <= 2^kMaxDigitBits) by one block of
+// kScatThreads threads; returns the total. Uses `tmp` (kScatThreads / 32 words).
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t *a, int n, uint32_t *tmp) {
+  constexpr int kPer = (1 << kMaxDigitBits) / kScatThreads;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int per = (n + kScatThreads - 1) / kScatThreads;  // <= kPer
+  uint32_t v[kPer], s = 0;
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) {
     const int j = t * per + i;
     v[i] = (i < per && j < n) ? a[j] : 0u;
     s += v[i];
@@ -106,13 +186,15 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t *a, int n, uint32_t
   if (lane == 31) tmp[warp] = inc;
   __syncthreads();
   uint32_t wpre = 0, tot = 0;
-  for (int w = 0; w < kBinThreads / 32; ++w) {
-    if (w < warp) wpre += tmp[w];
-    tot += tmp[w];
+#pragma unroll
+  for (int w = 0; w < kScatThreads / 32; ++w) {
+    const uint32_t x = tmp[w];
+    if (w < warp) wpre += x;
+    tot += x;
   }
   uint32_t run = wpre + inc - s;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
+  for (int i = 0; i < kPer; ++i) {
     const int j = t * per + i;
     if (i < per && j < n) {
       a[j] = run;
@@ -123,116 +205,153 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t *a, int n, uint32_t
   return tot;
 }
 
-// Stable scatter of one chunk: every kept element gets its rank among equal
-// digits earlier in the chunk (warp match + per-warp counters, as in the
-// histogram), is staged in shared memory in the chunk's digit order, and the
-// staged chunk is written out so that each digit's elements go to consecutive
-// addresses (coalesced runs) starting at that (digit, chunk)'s offset from the
-// scanned table. n_total: kept elements of the whole array (the table's sum).
+// Shared memory of k_scatter in 32-bit words: the ranking counters (16-bit,
+// one per warp and digit) share their space with the staged chunk (keys and
+// values), followed by two words per digit.
+__host__ __device__ constexpr int scatter_union_words(int nb) {
+  return (kScatThreads / 32) * nb / 2 > 2 * kBinChunk ? (kScatThreads / 32) * nb / 2
+                                                      : 2 * kBinChunk;
+}
+__host__ __device__ constexpr int scatter_smem_bytes(int nb) {
+  return (scatter_union_words(nb) + 2 * nb) * 4;
+}
+
+// Stable scatter of one chunk of 8192 elements. Warp w holds the chunk's
+// elements [512 w, 512 (w + 1)) as 16 rows of 32 consecutive elements (lane l
+// of row i: element 512 w + 32 i + l), so the order (warp, row, lane) is
+// input order. Ranking: row by row, each element's rank among the warp's
+// earlier elements of its digit is a per-warp counter (shared memory, 16 bits)
+// plus the number of lower lanes with the same digit (one ballot per bit); the
+// lowest such lane advances the counter. One pass over the digits then turns
+// the counters into the chunk positions (the digit's start in the chunk, from
+// the histogram table, plus the counts of the earlier warps), the elements are
+// staged in shared memory at their positions (the chunk in digit order), and
+// the staged chunk is written out so that consecutive slots of one digit go to
+// consecutive addresses, from the (digit, chunk)'s offset in the scanned table.
+// n_total: kept elements of the whole array (the table's sum).
 template <bool RAW>
-__global__ void __launch_bounds__(kBinThreads) k_scatter(
+__global__ void __launch_bounds__(kScatThreads, 2) k_scatter(
     RawIn raw, const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin,
     const uint32_t *__restrict__ n_total, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, const uint32_t *__restrict__ hscan, int64_t nchunks, int shift,
     int nb) {
+  constexpr int kWarps = kScatThreads / 32;
   extern __shared__ uint32_t sm[];
-  const int stride = nb + 1;
-  uint32_t *wcnt = sm;                 // [8][nb + 1] per-warp counts this round
-  uint32_t *run = wcnt + 8 * stride;   // [nb + 1] counts of earlier rounds
-  uint32_t *base = run + stride;       // [nb] global offset of (digit, chunk)
-  uint32_t *lst = base + nb;           // [nb] start of each digit in the staged chunk
-  uint32_t *sk = lst + nb;             // [kBinChunk] staged keys
-  uint32_t *sv = sk + kBinChunk;       // [kBinChunk] staged values
-  __shared__ uint32_t scan_tmp[kBinThreads / 32];
+  uint16_t *cnt = reinterpret_cast<uint16_t *>(sm);  // [kWarps][nb], then chunk positions
+  uint32_t *sk = sm;                                  // [kBinChunk] staged keys
+  uint32_t *sv = sm + kBinChunk;                      // [kBinChunk] staged values
+  uint32_t *lst = sm + scatter_union_words(nb);       // [nb] start of each digit in the chunk
+  uint32_t *gofs = lst + nb;                          // [nb] output offset minus the start
+  __shared__ uint32_t scan_tmp[kWarps];
   const int64_t n = RAW ? raw.n : (int64_t)*n_total;
   const int64_t chunk = blockIdx.x;
   const int64_t c0 = chunk * kBinChunk;
   if (c0 >= n) return;
   const int64_t ncells = (int64_t)nb * nchunks;
   const uint32_t total = *n_total;
-  for (int i = threadIdx.x; i < 9 * stride; i += blockDim.x) sm[i] = 0;
-  for (int d = threadIdx.x; d < nb; d += blockDim.x) {
+  for (int i = threadIdx.x; i < kWarps * nb / 2; i += kScatThreads) sm[i] = 0;
+  for (int d = threadIdx.x; d < nb; d += kScatThreads) {
     const int64_t cell = (int64_t)d * nchunks + chunk;
     const uint32_t b = hscan[cell];
-    base[d] = b;
+    gofs[d] = b;
     lst[d] = (cell + 1 < ncells ? hscan[cell + 1] : total) - b;  // this chunk's count of d
   }
   __syncthreads();
   const uint32_t m = block_excl_scan(lst, nb, scan_tmp);  // kept elements of the chunk
+  for (int d = threadIdx.x; d < nb; d += kScatThreads) gofs[d] -= lst[d];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1;
-  uint32_t *my = wcnt + warp * stride;
-  for (int r = 0; r < kBinRounds; ++r) {
-    uint32_t dg[kBinItems], kk[kBinItems], vv[kBinItems], rk[kBinItems];
+  uint16_t *my = cnt + warp * nb;
+  const uint32_t mask = (uint32_t)(nb - 1);
+  const int64_t wbase = c0 + (int64_t)warp * (32 * kScatItems) + lane;
+  // ps: two 16-bit ranks (then chunk positions, < 8192) per register
+  uint32_t kk[kScatItems], vv[kScatItems], ps[kScatItems / 2], ok = 0;
 #pragma unroll
-    for (int i = 0; i < kBinItems; ++i) {
-      int64_t e = c0 + (int64_t)r * (kBinThreads * kBinItems) + warp * (32 * kBinItems) + i * 32 +
-                  lane;
-      uint32_t d = (uint32_t)nb, key = 0, val = 0;
-      if (e < n) {
-        if (RAW) {
-          if (load_raw(raw, e, key, val)) d = (key >> shift) & (uint32_t)(nb - 1);
-        } else {
-          key = kin[e];
-          val = vin[e];
-          d = (key >> shift) & (uint32_t)(nb - 1);
-        }
-      }
-      uint32_t peers = __match_any_sync(0xffffffffu, d);
-      uint32_t before = __popc(peers & lt);
-      uint32_t cnt = my[d];
-      __syncwarp();
-      if (before == 0) my[d] = cnt + __popc(peers);
-      __syncwarp();
-      dg[i] = d;
-      kk[i] = key;
-      vv[i] = val;
-      rk[i] = cnt + before;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < kBinItems; ++i) {
-      uint32_t d = dg[i];
-      if (d < (uint32_t)nb) {
-        uint32_t pre = run[d] + rk[i];
-        for (int w2 = 0; w2 < warp; ++w2) pre += wcnt[w2 * stride + d];
-        const uint32_t slot = lst[d] + pre;
-        if (slot < (uint32_t)kBinChunk) {
-          sk[slot] = kk[i];
-          sv[slot] = vv[i];
-        }
+  for (int i = 0; i < kScatItems; ++i) {
+    const int64_t e = wbase + 32 * i;
+    uint32_t key = 0, val = 0;
+    bool kept = false;
+    if (e < n) {
+      if (RAW) {
+        kept = load_raw(raw, e, key, val);
+      } else {
+        key = kin[e];
+        val = vin[e];
+        kept = true;
       }
     }
-    __syncthreads();
-    for (int d = threadIdx.x; d < stride; d += blockDim.x) {
-      uint32_t s = 0;
-#pragma unroll
-      for (int w2 = 0; w2 < 8; ++w2) {
-        s += wcnt[w2 * stride + d];
-        wcnt[w2 * stride + d] = 0;
-      }
-      run[d] += s;
-    }
-    __syncthreads();
+    kk[i] = key;
+    vv[i] = val;
+    ok |= kept ? (1u << i) : 0u;
   }
+#pragma unroll
+  for (int i = 0; i < kScatItems; ++i) {
+    const bool kept = (ok >> i) & 1u;
+    const uint32_t d = kept ? (kk[i] >> shift) & mask : (uint32_t)nb;
+    // lanes with the same digit (kept ones) or the other dropped lanes: one
+    // ballot per digit bit
+    uint32_t peers = __ballot_sync(0xffffffffu, kept);
+    if (!kept) peers = ~peers;
+    for (int b = 0; (1 << b) < nb; ++b) {
+      const uint32_t bit = (d >> b) & 1u;
+      const uint32_t bm = __ballot_sync(0xffffffffu, bit);
+      peers &= bit ? bm : ~bm;
+    }
+    const uint32_t before = __popc(peers & lt);
+    uint32_t c = 0;
+    if (kept) c = my[d];
+    __syncwarp();
+    if (kept && before == 0) my[d] = (uint16_t)(c + __popc(peers));
+    __syncwarp();
+    const uint32_t r = c + before;
+    ps[i / 2] = (i & 1) ? (ps[i / 2] | (r << 16)) : r;
+  }
+  __syncthreads();
+  // counters -> chunk positions: start of the digit plus the earlier warps' counts
+  for (int d = threadIdx.x; d < nb; d += kScatThreads) {
+    uint32_t run = lst[d];
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+      const uint32_t v = cnt[w * nb + d];
+      cnt[w * nb + d] = (uint16_t)run;
+      run += v;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < kScatItems; ++i)
+    if ((ok >> i) & 1u) ps[i / 2] += (uint32_t)my[(kk[i] >> shift) & mask] << (16 * (i & 1));
+  __syncthreads();  // every counter read before the staged chunk overwrites them
+#pragma unroll
+  for (int i = 0; i < kScatItems; ++i) {
+    const uint32_t pos = (ps[i / 2] >> (16 * (i & 1))) & 0xffffu;
+    if (((ok >> i) & 1u) && pos < (uint32_t)kBinChunk) {
+      sk[pos] = kk[i];
+      sv[pos] = vv[i];
+    }
+  }
+  __syncthreads();
   // staged chunk out: consecutive slots of one digit go to consecutive addresses
-  for (uint32_t sl = threadIdx.x; sl < m && sl < (uint32_t)kBinChunk; sl += blockDim.x) {
+  for (uint32_t sl = threadIdx.x; sl < m && sl < (uint32_t)kBinChunk; sl += kScatThreads) {
     const uint32_t key = sk[sl];
-    const uint32_t d = (key >> shift) & (uint32_t)(nb - 1);
-    const uint32_t dest = base[d] + (sl - lst[d]);
-    kout[dest] = key;
-    vout[dest] = sv[sl];
+    const uint32_t dest = gofs[(key >> shift) & mask] + sl;
+    if (dest < total) {  // always true when the counts agree with the table
+      kout[dest] = key;
+      vout[dest] = sv[sl];
+    }
   }
 }
 
 // Segment bounds of the sorted keys: seg_lo[k] = first index, seg_hi[k] = one
 // past the last index of key k (both 0 for absent keys).
+// Keys at or beyond npx (impossible for a correct sort) are not written.
 __global__ void k_seg(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ n_dev,
-                      uint32_t *__restrict__ seg_lo, uint32_t *__restrict__ seg_hi) {
+                      uint32_t *__restrict__ seg_lo, uint32_t *__restrict__ seg_hi, int64_t npx) {
   const int64_t n = *n_dev;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     uint32_t k = keys[i];
+    if ((int64_t)k >= npx) continue;
     if (i == 0 || keys[i - 1] != k) seg_lo[k] = (uint32_t)i;
     if (i == n - 1 || keys[i + 1] != k) seg_hi[k] = (uint32_t)(i + 1);
   }
@@ -406,8 +525,24 @@ ddhf_status bin_core(Ctx *c, Slot &sl, const RawIn &raw, int n_min, int heavy_mi
       uint32_t *vo = last ? sl.ev : vbuf[pass & 1];
       const uint32_t *ki = pass ? kbuf[(pass - 1) & 1] : nullptr;
       const uint32_t *vi = pass ? vbuf[(pass - 1) & 1] : nullptr;
-      const size_t smem = (size_t)(9 * (nb + 1) + 2 * nb + 2 * kBinChunk) * sizeof(uint32_t);
-      if (pass == 0) {
+      const size_t smem = (size_t)scatter_smem_bytes(nb);
+      // raw events are packed by the first histogram into the second buffer
+      // pair (free until the second pass writes it) and sorted from there
+      RawIn in = raw;
+      if (pass == 0 && !raw.pk) {
+        const bool vec = (reinterpret_cast<uintptr_t>(raw.x) % 8 == 0) &&
+                         (reinterpret_cast<uintptr_t>(raw.y) % 8 == 0) &&
+                         (reinterpret_cast<uintptr_t>(raw.t) % 16 == 0) &&
+                         (reinterpret_cast<uintptr_t>(raw.p) % 4 == 0);
+        if (vec)
+          k_hist_pack<true><<<(unsigned)nch, kBinThreads, 0, s>>>(raw, c->keysB, c->valsB,
+                                                                  c->hist, nch, nb);
+        else
+          k_hist_pack<false><<<(unsigned)nch, kBinThreads, 0, s>>>(raw, c->keysB, c->valsB,
+                                                                   c->hist, nch, nb);
+        in.pk = c->keysB;
+        in.pv = c->valsB;
+      } else if (pass == 0) {
         k_hist<true><<<(unsigned)nch, kBinThreads, 0, s>>>(raw, nullptr, nullptr, c->hist, nch,
                                                            shift, nb);
       } else {
@@ -419,10 +554,10 @@ ddhf_status bin_core(Ctx *c, Slot &sl, const RawIn &raw, int n_min, int heavy_mi
       DDHF_CUDA_TRY(c, scan_rec<uint32_t>(c->hist, c->hist, (int64_t)nb * nch, c->scan_part,
                                           pass == 0 ? ntot : nullptr, s));
       if (pass == 0) {
-        k_scatter<true><<<(unsigned)nch, kBinThreads, smem, s>>>(raw, nullptr, nullptr, ntot, ko,
+        k_scatter<true><<<(unsigned)nch, kScatThreads, smem, s>>>(in, nullptr, nullptr, ntot, ko,
                                                                  vo, c->hist, nch, shift, nb);
       } else {
-        k_scatter<false><<<(unsigned)nch, kBinThreads, smem, s>>>(raw, ki, vi, ntot, ko, vo,
+        k_scatter<false><<<(unsigned)nch, kScatThreads, smem, s>>>(raw, ki, vi, ntot, ko, vo,
                                                                   c->hist, nch, shift, nb);
       }
       DDHF_CUDA_TRY(c, cudaGetLastError());
@@ -434,7 +569,7 @@ ddhf_status bin_core(Ctx *c, Slot &sl, const RawIn &raw, int n_min, int heavy_mi
   DDHF_CUDA_TRY(c, cudaMemsetAsync(c->seg_hi, 0, npx * sizeof(uint32_t), s));
   const int sm_blocks = c->num_sms * 8;
   if (nch > 0) {
-    k_seg<<<sm_blocks, 256, 0, s>>>(kfinal, ntot, c->seg_lo, c->seg_hi);
+    k_seg<<<sm_blocks, 256, 0, s>>>(kfinal, ntot, c->seg_lo, c->seg_hi, npx);
     DDHF_CUDA_TRY(c, cudaGetLastError());
   }
   unsigned pb = (unsigned)std::min<int64_t>(ceil_div(npx + 1, 256), sm_blocks);
@@ -469,8 +604,7 @@ ddhf_status bin_packed(Ctx *c, Slot &sl, const uint32_t *keys, const uint32_t *v
 }
 
 void set_bin_attributes() {
-  const int smem =
-      (9 * ((1 << kMaxDigitBits) + 1) + 2 * (1 << kMaxDigitBits) + 2 * kBinChunk) * sizeof(uint32_t);
+  const int smem = scatter_smem_bytes(1 << kMaxDigitBits);
   cudaFuncSetAttribute(k_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   cudaFuncSetAttribute(k_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }

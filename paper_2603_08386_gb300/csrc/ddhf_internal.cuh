@@ -15,10 +15,10 @@
 namespace ddhf {
 
 constexpr int kMaxDigitBits = 11;  // at most 2048 bins per radix pass
-constexpr int kBinThreads = 256;   // 8 warps per binning block
-constexpr int kBinItems = 8;       // items per lane per round
-constexpr int kBinRounds = 4;      // rounds per chunk
-constexpr int kBinChunk = kBinThreads * kBinItems * kBinRounds;  // 8192 events
+constexpr int kBinThreads = 256;   // threads of a histogram block (one chunk)
+constexpr int kScatThreads = 512;  // threads of a scatter block (one chunk, 16 warps)
+constexpr int kScatItems = 16;     // consecutive 32-event rows per scatter warp
+constexpr int kBinChunk = kScatThreads * kScatItems;  // 8192 events
 constexpr int kMaxBandWords = 8;   // comb rank band up to 256 positions
 constexpr uint32_t kSignBit = 0x80000000u;
 constexpr uint32_t kDropKey = 0xffffffffu;  // pre-packed sort input: pair not kept

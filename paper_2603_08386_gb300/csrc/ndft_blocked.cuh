@@ -155,13 +155,14 @@ struct Acc {
   }
 };
 
+// Events [e_lo, e_hi) of the staged chunk into the lane's tile.
 template <int TB>
-__device__ __forceinline__ void gemm_chunk(int ne, const float4 *stage, Acc<TB> &acc) {
+__device__ __forceinline__ void gemm_range(int e_lo, int e_hi, const float4 *stage, Acc<TB> &acc) {
   const int lane = threadIdx.x & 31;
   const int bg = lane >> 3, rg = lane & 7;
   const float4 *sb = stage + WarpLayout<TB>::kB + rg * 3;
   const float4 *sa = stage + WarpLayout<TB>::kA + bg * ALayout<TB>::kGroup;
-  for (int e = 0; e < ne; ++e) {
+  for (int e = e_lo; e < e_hi; ++e) {
     const float4 b01 = sb[e * kBEvent + 0];
     const float4 b23 = sb[e * kBEvent + 1];
     const float4 bs = sb[e * kBEvent + 2];
@@ -178,6 +179,11 @@ __device__ __forceinline__ void gemm_chunk(int ne, const float4 *stage, Acc<TB> 
       for (int h = 0; h < 2; ++h) acc.t3[i][h] = __ffma2_rn(ass, bss[h], acc.t3[i][h]);
     }
   }
+}
+
+template <int TB>
+__device__ __forceinline__ void gemm_chunk(int ne, const float4 *stage, Acc<TB> &acc) {
+  gemm_range<TB>(0, ne, stage, acc);
 }
 
 // Accumulate events [e_begin, e_end) of a pixel in steps of `estep` chunks
@@ -287,6 +293,124 @@ __device__ __forceinline__ void pixel_spectrum_warp(const BlockedArgs &A, const 
   }
 }
 
+// Power of the lane's tile straight to spectrum row `prow` (bin rows from b0):
+// lane (bg, rg) holds bins 32 (b0 + bg TB + i) + 4 rg + q, so each store of
+// the warp covers four whole 128-byte rows; bins at or beyond N are not written.
+template <int TB>
+__device__ __forceinline__ void store_tile(const BlockedArgs &A, const Acc<TB> &acc, int64_t prow,
+                                           int b0) {
+  const int lane = threadIdx.x & 31;
+  const int bg = lane >> 3, rg = lane & 7;
+  const int N = A.g.N;
+  float *dst = A.P + prow * A.ld;
+#pragma unroll
+  for (int i = 0; i < TB; ++i) {
+    float pv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float t1 = acc.get(0, i, q), t2 = acc.get(1, i, q), t3 = acc.get(2, i, q);
+      const float fr = __fsub_rn(t1, t2);
+      const float fi = __fsub_rn(__fsub_rn(t3, t1), t2);
+      pv[q] = __fmaf_rn(fr, fr, __fmul_rn(fi, fi));
+    }
+    const int j = 32 * (b0 + bg * TB + i) + 4 * rg;
+    if (A.vec_store && j + 3 < N) {
+      *reinterpret_cast<float4 *>(dst + j) = make_float4(pv[0], pv[1], pv[2], pv[3]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (j + q < N) dst[j + q] = pv[q];
+    }
+  }
+}
+
+// Light pixels of one slot, spectra to global memory. A warp takes runs of
+// kRun consecutive active pixels and, when their event lists follow one
+// another in memory (the CSR order of the binning), streams the run's events
+// through the 16-event factor chunks in that order: the factors of an event do
+// not depend on its pixel, so one chunk serves the end of one pixel and the
+// start of the next, and a pixel's tile is stored and cleared as soon as its
+// last event is in. Events of pixels outside the run's light set (heavy ones,
+// pixels left to the hybrid path, inactive pixels) are skipped chunk-wise.
+// Runs whose lists are not in order (caller-built lists) are streamed one
+// pixel at a time.
+template <int TB>
+__device__ __forceinline__ void light_stream(const BlockedArgs &A, float4 *stage) {
+  constexpr int kRun = 16;
+  const int lane = threadIdx.x & 31;
+  const int e = lane & 15;
+  const GridConst &g = A.g;
+  const SlotView &v = A.views[A.slot0];
+  const int64_t n_act = (int64_t)v.counters[2];
+  const int rows_per_pass = 4 * TB;
+  for (;;) {
+    uint32_t a0 = 0;
+    if (lane == 0) a0 = atomicAdd(&A.cursors[1], (uint32_t)kRun);
+    a0 = __shfl_sync(0xffffffffu, a0, 0);
+    if ((int64_t)a0 >= n_act) break;
+    // lane q < kRun: pixel a0 + q of the run, its event range and whether it is light
+    const int64_t aq = (int64_t)a0 + lane;
+    uint32_t q_lo = 0, q_hi = 0;
+    bool q_ok = false;
+    if (lane < kRun && aq < n_act) {
+      const uint32_t key = v.active[aq];
+      q_lo = v.offsets[key];
+      q_hi = v.offsets[key + 1];
+      const int cnt = (int)(q_hi - q_lo);
+      q_ok = cnt < A.heavy_min && !(A.skip_min > 0 && cnt >= A.skip_min);
+      if (q_ok && aq >= A.cap_px) {
+        raise_flag(A.flags, DDHF_FLAG_CAPACITY);
+        q_ok = false;
+      }
+    }
+    uint32_t okm = __ballot_sync(0xffffffffu, q_ok);
+    if (!okm) continue;
+    // in order: every light pixel's list starts at or after the previous one's end
+    const uint32_t lower = okm & lanemask_lt();
+    const int prev = lower ? 31 - __clz(lower) : -1;
+    const uint32_t prev_end = __shfl_sync(0xffffffffu, q_hi, prev < 0 ? 0 : prev);
+    const bool bad = q_ok && (q_hi < q_lo || (prev >= 0 && q_lo < prev_end));
+    const bool in_order = !__any_sync(0xffffffffu, bad);
+    // the whole run at once, or (lists out of order) one pixel at a time
+    for (uint32_t todo = okm; todo;) {
+      const uint32_t sub = in_order ? todo : (todo & (0u - todo));
+      todo &= ~sub;
+      const uint32_t e_end = __shfl_sync(0xffffffffu, q_hi, 31 - __clz(sub));
+      for (int b0 = 0; b0 < g.nbr; b0 += rows_per_pass) {
+        const uint64_t arow_mod[2] = {arow_residue(g, b0), arow_residue(g, b0 + 2 * TB)};
+        // the staged chunk holds events [c0, cend); wn: word of event cend + e
+        uint32_t c0 = 0, cend = 0, wn = 0;
+        bool have_wn = false;
+        for (uint32_t rem = sub; rem; rem &= rem - 1) {
+          const int p = __ffs(rem) - 1;
+          const uint32_t pe0 = __shfl_sync(0xffffffffu, q_lo, p);
+          const uint32_t pe1 = __shfl_sync(0xffffffffu, q_hi, p);
+          Acc<TB> acc;
+          acc.zero();
+          for (uint32_t pos = pe0; pos < pe1;) {
+            if (pos >= cend) {  // stage the chunk that starts at pos
+              const uint32_t w =
+                  have_wn && pos == cend ? wn : (pos + e < e_end ? v.ev[pos + e] : 0u);
+              c0 = pos;
+              cend = min(c0 + (uint32_t)kGenChunk, e_end);
+              __syncwarp();  // the previous chunk's products are done
+              gen_chunk<TB>(w, c0 + e < cend, g, arow_mod, stage);
+              __syncwarp();
+              wn = cend + e < e_end ? v.ev[cend + e] : 0u;
+              have_wn = true;
+            }
+            const uint32_t e1 = min(pe1, cend);
+            gemm_range<TB>((int)(pos - c0), (int)(e1 - c0), stage, acc);
+            pos = e1;
+          }
+          store_tile<TB>(A, acc, (int64_t)a0 + p, b0);
+        }
+        __syncwarp();
+      }
+    }
+  }
+}
+
 template <int NW>
 __device__ __forceinline__ void store_scores(const BlockedArgs &A, const SlotView &v, int64_t a,
                                              uint32_t key, const CombOut &o) {
@@ -300,7 +424,7 @@ __device__ __forceinline__ void store_scores(const BlockedArgs &A, const SlotVie
 }
 
 template <int TB, int NW, bool FUSED>
-__global__ void k_blocked(BlockedArgs A) {
+__global__ void __launch_bounds__(256, TB == 6 ? 2 : 1) k_blocked(BlockedArgs A) {
   extern __shared__ float4 smem4[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int warp_f4 = A.warp_bytes / 16;
@@ -377,6 +501,11 @@ __global__ void k_blocked(BlockedArgs A) {
       store_scores<NW>(A, v, a, key, o);
     }
     __syncthreads();
+  }
+
+  if constexpr (!FUSED) {
+    light_stream<TB>(A, stage);
+    return;
   }
 
   // ---------------- light pixels: one warp each, virtual index over slots x pixels.
