@@ -57,7 +57,7 @@ OPS_PER_TERM = 3  # FP32 FMA-pipe lane-ops per term of the blocked three-multipl
 # of the kernel on a 640x360 window of the same recipe (profiles/), scaled to a
 # launch by its active pixels (the traffic is per-pixel rows). A figure is
 # listed only while the kernel is the one that was captured.
-TRAFFIC_PER_PIXEL = {"k_comb<2>": 3044.0}
+TRAFFIC_PER_PIXEL = {"k_comb<2>": 3044.0, "k_blocked<6,1,0>": 2898.0}
 TRAFFIC_NOTE = ("null: the ncu DRAM capture of this kernel predates its current code "
                 "(profiles/ keeps the earlier figure)")
 
@@ -759,8 +759,10 @@ def main():
         kern += " with the hybrid grid kernels (spectrum stage time)"
     n_act = sum(active_of(w, W, H) for w in wins)
     tb = 6 if nb <= 768 and nb > 512 else None  # rows per lane the launcher picks for 750 bins
+    # the captured traffic is that of the blocked kernel on every active pixel
+    blocked_alone = not fused_mode and (not hybrid_on or bool(forms))
     tr_ndft = (TRAFFIC_PER_PIXEL["k_blocked<6,1,0>"] * n_act / nwin
-               if ("k_blocked<6,1,0>" in TRAFFIC_PER_PIXEL and not fused_mode and tb == 6
+               if ("k_blocked<6,1,0>" in TRAFFIC_PER_PIXEL and blocked_alone and tb == 6
                    and int(tuning.get("rows_per_lane", 0)) in (0, 6))
                else None)
     roof_ndft = dict(bound="alu", achieved=achieved, peak=peak, unit="Tops/s",

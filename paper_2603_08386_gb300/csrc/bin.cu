@@ -207,46 +207,76 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t *a, int n, uint32_t
 
 // Shared memory of k_scatter in 32-bit words: the ranking counters (16-bit,
 // one per warp and digit) share their space with the staged chunk (keys and
-// values), followed by two words per digit.
+// values), followed by two words per digit and the chunk's values in input
+// order.
 __host__ __device__ constexpr int scatter_union_words(int nb) {
   return (kScatThreads / 32) * nb / 2 > 2 * kBinChunk ? (kScatThreads / 32) * nb / 2
                                                       : 2 * kBinChunk;
 }
 __host__ __device__ constexpr int scatter_smem_bytes(int nb) {
-  return (scatter_union_words(nb) + 2 * nb) * 4;
+  return (scatter_union_words(nb) + 2 * nb + kBinChunk) * 4;
 }
 
-// Stable scatter of one chunk of 8192 elements. Warp w holds the chunk's
-// elements [512 w, 512 (w + 1)) as 16 rows of 32 consecutive elements (lane l
-// of row i: element 512 w + 32 i + l), so the order (warp, row, lane) is
-// input order. Ranking: row by row, each element's rank among the warp's
-// earlier elements of its digit is a per-warp counter (shared memory, 16 bits)
-// plus the number of lower lanes with the same digit (one ballot per bit); the
-// lowest such lane advances the counter. One pass over the digits then turns
-// the counters into the chunk positions (the digit's start in the chunk, from
-// the histogram table, plus the counts of the earlier warps), the elements are
-// staged in shared memory at their positions (the chunk in digit order), and
-// the staged chunk is written out so that consecutive slots of one digit go to
-// consecutive addresses, from the (digit, chunk)'s offset in the scanned table.
-// n_total: kept elements of the whole array (the table's sum).
-template <bool RAW>
+// Asynchronous global -> shared copies (cp.async), `bytes` of `size` read.
+__device__ __forceinline__ void cp_async16(uint32_t dst_sa, const void *src, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst_sa), "l"(src),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(uint32_t dst_sa, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst_sa), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// Stable scatter of one chunk of 8192 (key, value) elements. Warp w holds the
+// chunk's keys [512 w, 512 (w + 1)) as 16 rows of 32 consecutive keys (lane l
+// of row i: element 512 w + 32 i + l), so the order (warp, row, lane) is input
+// order; the values go to shared memory in input order by asynchronous copies
+// meanwhile. Ranking: row by row, each element's rank among the warp's earlier
+// elements of its digit is a per-warp counter (shared memory, 16 bits) plus
+// the number of lower lanes with the same digit (one ballot per digit bit);
+// the lowest such lane advances the counter. One pass over the digits then
+// turns the counters into the chunk positions (the digit's start in the
+// chunk, from the histogram table, plus the counts of the earlier warps), the
+// elements are staged in shared memory at their positions (the chunk in digit
+// order), and the staged chunk is written out so that consecutive slots of one
+// digit go to consecutive addresses, from the (digit, chunk)'s offset in the
+// scanned table. DROP (first pass): the input has n_in elements, key kDropKey
+// marks one that is not kept; otherwise all n_total elements are kept.
+// n_total: kept elements of the whole array (the table's sum). BITS: digit
+// width (nb = 2^BITS), a template argument so that the ballots unroll.
+template <bool DROP, int BITS>
 __global__ void __launch_bounds__(kScatThreads, 2) k_scatter(
-    RawIn raw, const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin,
+    const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, int64_t n_in,
     const uint32_t *__restrict__ n_total, uint32_t *__restrict__ kout,
-    uint32_t *__restrict__ vout, const uint32_t *__restrict__ hscan, int64_t nchunks, int shift,
-    int nb) {
+    uint32_t *__restrict__ vout, const uint32_t *__restrict__ hscan, int64_t nchunks,
+    int shift) {
   constexpr int kWarps = kScatThreads / 32;
+  constexpr int nb = 1 << BITS;
+  constexpr uint32_t mask = (uint32_t)(nb - 1);
   extern __shared__ uint32_t sm[];
   uint16_t *cnt = reinterpret_cast<uint16_t *>(sm);  // [kWarps][nb], then chunk positions
   uint32_t *sk = sm;                                  // [kBinChunk] staged keys
   uint32_t *sv = sm + kBinChunk;                      // [kBinChunk] staged values
   uint32_t *lst = sm + scatter_union_words(nb);       // [nb] start of each digit in the chunk
   uint32_t *gofs = lst + nb;                          // [nb] output offset minus the start
+  uint32_t *vbuf = gofs + nb;                         // [kBinChunk] values in input order
   __shared__ uint32_t scan_tmp[kWarps];
-  const int64_t n = RAW ? raw.n : (int64_t)*n_total;
+  const int64_t n = DROP ? n_in : (int64_t)*n_total;
   const int64_t chunk = blockIdx.x;
   const int64_t c0 = chunk * kBinChunk;
   if (c0 >= n) return;
+  const int nloc = (int)min((int64_t)kBinChunk, n - c0);  // elements of this chunk
+  // values -> vbuf (16-byte copies when the array is aligned for them)
+  const uint32_t vbuf_sa = (uint32_t)__cvta_generic_to_shared(vbuf);
+  if ((reinterpret_cast<uintptr_t>(vin) & 15) == 0) {
+    for (int q = threadIdx.x; 4 * q < nloc; q += kScatThreads)
+      cp_async16(vbuf_sa + 16 * q, vin + c0 + 4 * q, 4 * min(4, nloc - 4 * q));
+  } else {
+    for (int q = threadIdx.x; q < nloc; q += kScatThreads) cp_async4(vbuf_sa + 4 * q, vin + c0 + q);
+  }
   const int64_t ncells = (int64_t)nb * nchunks;
   const uint32_t total = *n_total;
   for (int i = threadIdx.x; i < kWarps * nb / 2; i += kScatThreads) sm[i] = 0;
@@ -262,40 +292,29 @@ __global__ void __launch_bounds__(kScatThreads, 2) k_scatter(
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1;
   uint16_t *my = cnt + warp * nb;
-  const uint32_t mask = (uint32_t)(nb - 1);
-  const int64_t wbase = c0 + (int64_t)warp * (32 * kScatItems) + lane;
+  const int wloc = warp * (32 * kScatItems) + lane;  // local index of row 0
   // ps: two 16-bit ranks (then chunk positions, < 8192) per register
-  uint32_t kk[kScatItems], vv[kScatItems], ps[kScatItems / 2], ok = 0;
+  uint32_t kk[kScatItems], ps[kScatItems / 2], ok = 0;
 #pragma unroll
   for (int i = 0; i < kScatItems; ++i) {
-    const int64_t e = wbase + 32 * i;
-    uint32_t key = 0, val = 0;
-    bool kept = false;
-    if (e < n) {
-      if (RAW) {
-        kept = load_raw(raw, e, key, val);
-      } else {
-        key = kin[e];
-        val = vin[e];
-        kept = true;
-      }
-    }
+    const int l = wloc + 32 * i;
+    const uint32_t key = l < nloc ? kin[c0 + l] : kDropKey;
+    const bool kept = l < nloc && (!DROP || key != kDropKey);
     kk[i] = key;
-    vv[i] = val;
     ok |= kept ? (1u << i) : 0u;
   }
 #pragma unroll
   for (int i = 0; i < kScatItems; ++i) {
     const bool kept = (ok >> i) & 1u;
-    const uint32_t d = kept ? (kk[i] >> shift) & mask : (uint32_t)nb;
-    // lanes with the same digit (kept ones) or the other dropped lanes: one
-    // ballot per digit bit
+    const uint32_t d = (kk[i] >> shift) & mask;
+    // lanes with the same digit (kept ones) or the other dropped lanes
     uint32_t peers = __ballot_sync(0xffffffffu, kept);
     if (!kept) peers = ~peers;
-    for (int b = 0; (1 << b) < nb; ++b) {
+#pragma unroll
+    for (int b = 0; b < BITS; ++b) {
       const uint32_t bit = (d >> b) & 1u;
       const uint32_t bm = __ballot_sync(0xffffffffu, bit);
-      peers &= bit ? bm : ~bm;
+      peers &= bm ^ (bit - 1u);  // bm where the bit is set, ~bm where it is not
     }
     const uint32_t before = __popc(peers & lt);
     uint32_t c = 0;
@@ -321,13 +340,14 @@ __global__ void __launch_bounds__(kScatThreads, 2) k_scatter(
 #pragma unroll
   for (int i = 0; i < kScatItems; ++i)
     if ((ok >> i) & 1u) ps[i / 2] += (uint32_t)my[(kk[i] >> shift) & mask] << (16 * (i & 1));
-  __syncthreads();  // every counter read before the staged chunk overwrites them
+  cp_async_wait_all();
+  __syncthreads();  // counters read, values arrived
 #pragma unroll
   for (int i = 0; i < kScatItems; ++i) {
     const uint32_t pos = (ps[i / 2] >> (16 * (i & 1))) & 0xffffu;
     if (((ok >> i) & 1u) && pos < (uint32_t)kBinChunk) {
       sk[pos] = kk[i];
-      sv[pos] = vv[i];
+      sv[pos] = vbuf[wloc + 32 * i];
     }
   }
   __syncthreads();
@@ -504,6 +524,29 @@ ddhf_status launch_scan_u64(Ctx *c, const uint64_t *in, uint64_t *out, int64_t n
   return DDHF_OK;
 }
 
+// k_scatter for a digit width of `bits` (1..kMaxDigitBits).
+template <bool DROP, int BITS = 1>
+void launch_scatter(int bits, int64_t nch, cudaStream_t s, const uint32_t *kin,
+                    const uint32_t *vin, int64_t n_in, const uint32_t *n_total, uint32_t *kout,
+                    uint32_t *vout, const uint32_t *hscan, int shift) {
+  if constexpr (BITS <= kMaxDigitBits) {
+    if (bits != BITS)
+      return launch_scatter<DROP, BITS + 1>(bits, nch, s, kin, vin, n_in, n_total, kout, vout,
+                                            hscan, shift);
+    k_scatter<DROP, BITS><<<(unsigned)nch, kScatThreads, scatter_smem_bytes(1 << BITS), s>>>(
+        kin, vin, n_in, n_total, kout, vout, hscan, nch, shift);
+  }
+}
+
+template <bool DROP, int BITS = 1>
+void scatter_attributes() {
+  if constexpr (BITS <= kMaxDigitBits) {
+    cudaFuncSetAttribute(k_scatter<DROP, BITS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         scatter_smem_bytes(1 << BITS));
+    scatter_attributes<DROP, BITS + 1>();
+  }
+}
+
 ddhf_status bin_core(Ctx *c, Slot &sl, const RawIn &raw, int n_min, int heavy_min,
                      uint64_t *heavy_list, uint32_t *heavy_count, uint32_t slot_tag,
                      int64_t heavy_cap, cudaStream_t s) {
@@ -525,7 +568,6 @@ ddhf_status bin_core(Ctx *c, Slot &sl, const RawIn &raw, int n_min, int heavy_mi
       uint32_t *vo = last ? sl.ev : vbuf[pass & 1];
       const uint32_t *ki = pass ? kbuf[(pass - 1) & 1] : nullptr;
       const uint32_t *vi = pass ? vbuf[(pass - 1) & 1] : nullptr;
-      const size_t smem = (size_t)scatter_smem_bytes(nb);
       // raw events are packed by the first histogram into the second buffer
       // pair (free until the second pass writes it) and sorted from there
       RawIn in = raw;
@@ -553,13 +595,10 @@ ddhf_status bin_core(Ctx *c, Slot &sl, const RawIn &raw, int n_min, int heavy_mi
       // pass 0: the grand total of the table is the number of kept events
       DDHF_CUDA_TRY(c, scan_rec<uint32_t>(c->hist, c->hist, (int64_t)nb * nch, c->scan_part,
                                           pass == 0 ? ntot : nullptr, s));
-      if (pass == 0) {
-        k_scatter<true><<<(unsigned)nch, kScatThreads, smem, s>>>(in, nullptr, nullptr, ntot, ko,
-                                                                 vo, c->hist, nch, shift, nb);
-      } else {
-        k_scatter<false><<<(unsigned)nch, kScatThreads, smem, s>>>(raw, ki, vi, ntot, ko, vo,
-                                                                  c->hist, nch, shift, nb);
-      }
+      if (pass == 0)
+        launch_scatter<true>(bits, nch, s, in.pk, in.pv, n, ntot, ko, vo, c->hist, shift);
+      else
+        launch_scatter<false>(bits, nch, s, ki, vi, n, ntot, ko, vo, c->hist, shift);
       DDHF_CUDA_TRY(c, cudaGetLastError());
       shift += bits;
     }
@@ -604,9 +643,8 @@ ddhf_status bin_packed(Ctx *c, Slot &sl, const uint32_t *keys, const uint32_t *v
 }
 
 void set_bin_attributes() {
-  const int smem = scatter_smem_bytes(1 << kMaxDigitBits);
-  cudaFuncSetAttribute(k_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  cudaFuncSetAttribute(k_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  scatter_attributes<true>();
+  scatter_attributes<false>();
 }
 
 }  // namespace ddhf
