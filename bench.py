@@ -75,6 +75,72 @@ def _gen_c4(b):
     return sc.x, sc.y, sc.t, sc.p, sc.t0, sc.window_us, sc.n
 
 
+# thresholds inside Table 2's ranges that separate synthetic drones from the C3
+# noise (Table 2's own tau_sf and tau_comb flag most noise pixels of these
+# dense windows, so detection there yields one sensor-wide box)
+LABELLED_PARAMS = dict(tau_sf=0.5, tau_comb=2.0, M=4, d=3, h_min=4, n_min=6, A_min=25,
+                       alpha=2.0)
+LABELLED_SEEDS = (400, 302, 401)
+
+
+def _gen_labelled(seed):
+    # a full-size labelled window: the C3 noise recipe with 1-3 drones
+    s = synth.labelled_scene(seed, W=1280, H=720, min_sep=100)
+    return (s.x, s.y, s.t, s.p, s.t0, s.window_us, s.n,
+            [d["box"] for d in s.drones if d["box"] is not None])
+
+
+def _iou(a, b):
+    ix = min(a[2], b[2]) - max(a[0], b[0]) + 1
+    iy = min(a[3], b[3]) - max(a[1], b[1]) + 1
+    if ix <= 0 or iy <= 0:
+        return 0.0
+    inter = ix * iy
+    area = lambda r: (r[2] - r[0] + 1) * (r[3] - r[1] + 1)
+    return inter / (area(a) + area(b) - inter)
+
+
+def labelled_leg(scenes, W, H, grid, tuning, torch, ddhf, replays=100):
+    """Detection on full-size labelled windows (synth.labelled_scene) with
+    thresholds that separate the drones: the graph-replayed one-window call
+    timed replay by replay, and what it found (boxes, rotor pixels, ground-truth
+    drones matched at IoU >= 0.5, the paper's matching rule)."""
+    rows = []
+    for (x, y, t, p, t0, win, n, gt) in scenes:
+        c = ddhf.Context(W, H, grid, ddhf.default_params(**LABELLED_PARAMS), max_events=max(n, 1),
+                         max_windows=1)
+        c.set_tuning(**{k: v for k, v in tuning.items() if k != "how"})
+        d = [torch.from_numpy(a).cuda() for a in (x, y, t, p)]
+        wl = [(d[0], d[1], d[2], d[3], n, t0, win)]
+        bx = torch.empty((256, 5), dtype=torch.int32, device="cuda")
+        nb = torch.zeros(1, dtype=torch.int32, device="cuda")
+        for _ in range(5):
+            ddhf.ddhf_detect_batch(c.h, wl, bx, 256, nb, None, use_graph=True)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(replays)]
+        for a, b in evs:
+            a.record()
+            ddhf.ddhf_detect_batch(c.h, wl, bx, 256, nb, None, use_graph=True)
+            b.record()
+        torch.cuda.synchronize()
+        lt = np.array([a.elapsed_time(b) for a, b in evs])
+        k = int(nb.item())
+        boxes = bx[:min(k, 256)].cpu().numpy()
+        st = c.stats()
+        c.close()
+        matched = sum(1 for g in gt if any(_iou(g, b[:4]) >= 0.5 for b in boxes))
+        true_boxes = sum(1 for b in boxes if any(_iou(g, b[:4]) >= 0.5 for g in gt))
+        q25, q50, q75, q95 = np.percentile(lt, [25, 50, 75, 95])
+        rows.append(dict(events=int(n), active_pixels=int(st["n_active"]),
+                         rotor_pixels=int(st["n_rotor"]), boxes=k, drones=len(gt),
+                         drones_matched=matched, boxes_matching_a_drone=true_boxes,
+                         median_ms=float(q50), iqr_ms=float(q75 - q25), p95_ms=float(q95)))
+    return dict(window=f"{W}x{H}, 30 ms labelled windows (C3 noise recipe, 1-3 drones), seeds "
+                       f"{list(LABELLED_SEEDS)}; {replays} graph replays each",
+                params=LABELLED_PARAMS, points=rows)
+
+
 def slide_leg(wins, W, H, grid, torch, ddhf, hop_us=3750, rebuild_every=64, cap_box=256,
               warm_passes=2):
     """The sliding window on one C3 stream (consecutive windows of stream 0):
@@ -416,13 +482,15 @@ def main():
     ap.add_argument("--no-sweep", action="store_true",
                     help="skip the one-window latency at lower event densities")
     ap.add_argument("--no-softcomb", action="store_true", help="skip the soft-comb timing")
+    ap.add_argument("--no-labelled", action="store_true",
+                    help="skip the detection on labelled windows")
     ap.add_argument("--no-slide", action="store_true", help="skip the sliding-window timing")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the one-window blocked / hybrid spectrum timing")
     ap.add_argument("--only-slide", action="store_true",
                     help="run only the sliding-window leg and print its object (profiling)")
     ap.add_argument("--slide-warm", type=int, default=2, help="untimed sliding-window passes")
-    ap.add_argument("--softcomb-windows", type=int, default=2)
+    ap.add_argument("--softcomb-windows", type=int, default=16)
     ap.add_argument("--latency-replays", type=int, default=100)
     ap.add_argument("--sensor", default="1280x720",
                     help="WxH of the synthetic sensor (smaller sizes for profiling captures)")
@@ -441,6 +509,10 @@ def main():
         with mp.get_context("spawn").Pool(processes=max(1, min(args.procs,
                                                                   args.softcomb_windows))) as pool:
             c4 = pool.map(_gen_c4, range(args.softcomb_windows))
+    lab = []
+    if not args.no_labelled and rank == 0 and (W, H) == (1280, 720):
+        with mp.get_context("spawn").Pool(processes=len(LABELLED_SEEDS)) as pool:
+            lab = pool.map(_gen_labelled, LABELLED_SEEDS)
 
     import torch
     from paper_2603_08386_gb300 import build, ddhf
@@ -590,6 +662,10 @@ def main():
     if not args.no_sweep and rank == 0:
         sweep = latency_sweep((1.0, 2.0, 3.0, 5.0, 10.0), W, H, grid, tuning, torch, ddhf,
                               replays=args.latency_replays)
+    labelled = None
+    if lab:
+        labelled = labelled_leg(lab, W, H, grid, tuning, torch, ddhf, replays=args.latency_replays)
+        del lab
     # ------------------------------------------------------------ spectrum forms, one window
     # window 0 alone through ddhf_power_spectrum: the blocked kernel on every
     # active pixel (the FMA-pipe roofline of that kernel, without the hybrid
@@ -640,55 +716,62 @@ def main():
         if lat:
             slide["full_window_ms_median"] = lat["median_ms"]
     # ------------------------------------------------------------ soft comb and its adjoint
-    # every active pixel of each 640x480 window: S and dS/d(f0, w, sigma) for
-    # 6 harmonics x (2Q+1) = 42 evaluation frequencies per pixel
+    # C4: a batch of 640x480 windows (16 by default) laid out as one window of
+    # a 640 x (16 * 480) sensor (ddhf.stack_windows), binned once; one
+    # ddhf_softcomb call scores every active pixel of the batch (S), one more
+    # gives dS/d(f0, w, sigma), for 6 harmonics x (2Q+1) = 42 evaluation
+    # frequencies per pixel
     softc = None
     if c4:
         Q, delta, n_h = 3, 2.0, 6
-        fw_ms, bw_ms, terms_sc, pix_sc = [], [], 0, 0
-        gen = torch.Generator(device="cuda").manual_seed(1004)
-        for (x4, y4, t4, p4, t04, w4, n4) in c4:
-            cc = ddhf.Context(640, 480, grid, max_events=n4)
-            d4 = [torch.from_numpy(a).cuda() for a in (x4, y4, t4, p4)]
-            cc.bin_events(*d4, t04, w4)
-            csr = cc.csr()
-            pix = csr["active"]
-            na = pix.numel()
-            offs = csr["offsets"].long()
-            cnt = int((offs[pix.long() + 1] - offs[pix.long()]).sum().item())
-            f0 = 50.0 + 150.0 * torch.rand(na, device="cuda", generator=gen)
-            wv = torch.ones(n_h, device="cuda")
-            sg = torch.full((n_h,), 2.0, device="cuda")
-            Bv = torch.ones(na, device="cuda")
-            Sv = torch.empty(na, device="cuda")
-            gS = torch.ones(na, device="cuda")
-            gf, gw, gsg = torch.empty(na, device="cuda"), torch.empty(n_h, device="cuda"), \
-                torch.empty(n_h, device="cuda")
-            fwd = lambda: ddhf.ddhf_softcomb(cc.h, pix, f0, n_h, Q, delta, w4 / 2, wv, sg, Bv, S=Sv)
-            bwd = lambda: ddhf.ddhf_softcomb(cc.h, pix, f0, n_h, Q, delta, w4 / 2, wv, sg, Bv,
-                                             grad_S=gS, grad_f0=gf, grad_w=gw, grad_sigma=gsg)
-            for fn, acc in ((fwd, fw_ms), (bwd, bw_ms)):
-                fn()
-                torch.cuda.synchronize()
-                a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a0.record()
-                for _ in range(5):
-                    fn()
-                a1.record()
-                torch.cuda.synchronize()
-                acc.append(a0.elapsed_time(a1) / 5)
-            cc.stats()
-            cc.close()
-            terms_sc += cnt * n_h * (2 * Q + 1)
-            pix_sc += na
         nwc = len(c4)
-        softc = dict(workload=f"{nwc} windows of 640x480, 40 ms (C2 density), 750-bin grid; "
-                              "all active pixels; 6 harmonics, Q=3, delta 2 Hz",
-                     pixels=pix_sc, terms=terms_sc,
-                     fwd_ms_per_window=statistics.mean(fw_ms),
-                     bwd_ms_per_window=statistics.mean(bw_ms),
-                     fwd_terms_per_s=terms_sc / (sum(fw_ms) * 1e-3),
-                     bwd_terms_per_s=terms_sc / (sum(bw_ms) * 1e-3),
+        w4 = c4[0][5]
+        xs, ys, ts, ps = ddhf.stack_windows([(a[0], a[1], a[2], a[3], a[4]) for a in c4], 480)
+        n4 = int(xs.size)
+        cc = ddhf.Context(640, 480 * nwc, grid, max_events=n4)
+        d4 = [torch.from_numpy(a).cuda() for a in (xs, ys, ts, ps)]
+        cc.bin_events(*d4, 0, w4)
+        csr = cc.csr()
+        pix = csr["active"]
+        na = pix.numel()
+        offs = csr["offsets"].long()
+        cnt = int((offs[pix.long() + 1] - offs[pix.long()]).sum().item())
+        gen = torch.Generator(device="cuda").manual_seed(1004)
+        f0 = 50.0 + 150.0 * torch.rand(na, device="cuda", generator=gen)
+        wv = torch.ones(n_h, device="cuda")
+        sg = torch.full((n_h,), 2.0, device="cuda")
+        Bv = torch.ones(na, device="cuda")
+        Sv = torch.empty(na, device="cuda")
+        gS = torch.ones(na, device="cuda")
+        gf, gw, gsg = torch.empty(na, device="cuda"), torch.empty(n_h, device="cuda"), \
+            torch.empty(n_h, device="cuda")
+        fwd = lambda: ddhf.ddhf_softcomb(cc.h, pix, f0, n_h, Q, delta, w4 / 2, wv, sg, Bv, S=Sv)
+        bwd = lambda: ddhf.ddhf_softcomb(cc.h, pix, f0, n_h, Q, delta, w4 / 2, wv, sg, Bv,
+                                         grad_S=gS, grad_f0=gf, grad_w=gw, grad_sigma=gsg)
+        timed = {}
+        for name, fn in (("fwd", fwd), ("bwd", bwd)):
+            fn()
+            torch.cuda.synchronize()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record()
+            for _ in range(5):
+                fn()
+            a1.record()
+            torch.cuda.synchronize()
+            timed[name] = a0.elapsed_time(a1) / 5
+        cc.stats()
+        cc.close()
+        del d4
+        terms_sc = cnt * n_h * (2 * Q + 1)
+        softc = dict(workload=f"C4: {nwc} windows of 640x480, 40 ms (C2 density), 750-bin grid, "
+                              "stacked into one 640x" + str(480 * nwc) + " window; every active "
+                              "pixel; 6 harmonics, Q=3, delta 2 Hz; one call per direction",
+                     windows=nwc, events=n4, pixels=na, terms=terms_sc,
+                     fwd_ms_per_call=timed["fwd"], bwd_ms_per_call=timed["bwd"],
+                     fwd_ms_per_window=timed["fwd"] / nwc,
+                     bwd_ms_per_window=timed["bwd"] / nwc,
+                     fwd_terms_per_s=terms_sc / (timed["fwd"] * 1e-3),
+                     bwd_terms_per_s=terms_sc / (timed["bwd"] * 1e-3),
                      unit="event x evaluation-frequency terms/s")
     # ------------------------------------------------------------ plain per-pixel pipeline
     plain = None
@@ -828,6 +911,7 @@ def main():
         e2e=e2e,
         window_latency=lat,
         latency_sweep=sweep,
+        labelled=labelled,
         peaks=dict(peaks, unit="per second, whole device",
                    how="ddhf_measure_pipes: 8 independent chains per thread, 8 blocks of "
                        "256 threads per SM, CUDA events"),

@@ -16,6 +16,7 @@ the passage of arXiv 2603.08386 it restates:
   comb, comb_f32  Sec. 3.4 Eq. 8-11
   ccl8            Sec. 3.5 "Segmentation mask processing"
   boxes           Sec. 3.5 and Eq. 12
+  box_frequencies Eq. 11 (dominant frequency of rotor pixels) per detection
   classify        Sec. 3.5 per-pixel pipeline (Eq. 6-11)
   softcomb        soft comb score and its gradients (differentiation pattern)
 """
@@ -255,3 +256,26 @@ def softcomb(tau, pol, f0, w, sigma, delta, Q, B, tau_c=0.0):
                             _ptr(gf))
     return dict(S=float(S), dS_df0=float(g0[0]), dS_dw=gw, dS_dsigma=gs,
                 dS_df=gf.reshape(nh, 2 * int(Q) + 1))
+
+
+def box_frequencies(boxes, active, mask, snr, f0_bin, W):
+    """Eq. 11 returns a dominant frequency per rotor pixel; a detection box
+    takes that of its strongest rotor pixel: for each box (x0, y0, x1, y1,
+    inclusive bounds), among the active pixels (keys y*W + x, ascending, with
+    snr and f0_bin in active order) whose mask entry is set and whose (x, y)
+    lies in the box, the largest SNR, ties to the smallest key. Returns
+    (f0_bin, snr) per box, (-1, 0.0) for a box without rotor pixels."""
+    active = np.asarray(active, np.int64)
+    ys, xs = active // W, active % W
+    rot = np.asarray(mask, bool)[active]
+    out_f, out_s = [], []
+    for b in np.asarray(boxes).reshape(-1, np.asarray(boxes).shape[-1]):
+        x0, y0, x1, y1 = (int(v) for v in b[:4])
+        best = -1
+        for i in range(active.size):
+            if rot[i] and x0 <= xs[i] <= x1 and y0 <= ys[i] <= y1:
+                if best < 0 or snr[i] > snr[best]:  # first index wins ties
+                    best = i
+        out_f.append(int(f0_bin[best]) if best >= 0 else -1)
+        out_s.append(float(snr[best]) if best >= 0 else 0.0)
+    return np.array(out_f, np.int32), np.array(out_s, np.float32)

@@ -69,6 +69,20 @@ __global__ void __launch_bounds__(kBinThreads) k_hist(RawIn raw, const uint32_t 
   for (int d = threadIdx.x; d < nb; d += blockDim.x) sh[d] = 0;
   __syncthreads();
   const int64_t c1 = min(n, c0 + (int64_t)kBinChunk);
+  if (!RAW && c1 - c0 == kBinChunk && (reinterpret_cast<uintptr_t>(kin) & 15) == 0) {
+    // a whole chunk of sort words: 16-byte loads, 4 keys each, 8 per thread and step
+    const uint4 *k4 = reinterpret_cast<const uint4 *>(kin + c0);
+    for (int q = threadIdx.x; q < kBinChunk / 4; q += 2 * kBinThreads) {
+      const uint4 a = k4[q];
+      const uint4 b = k4[q + kBinThreads];
+      const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int u = 0; u < 8; ++u) atomicAdd(&sh[(w[u] >> shift) & (uint32_t)(nb - 1)], 1u);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < nb; d += blockDim.x) hist[(int64_t)d * nchunks + chunk] = sh[d];
+    return;
+  }
   for (int64_t base = c0 + threadIdx.x; base < c1; base += (int64_t)kBinThreads * kU) {
     uint32_t d[kU];
 #pragma unroll
@@ -209,9 +223,14 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t *a, int n, uint32_t
 // one per warp and digit) share their space with the staged chunk (keys and
 // values), followed by two words per digit and the chunk's values in input
 // order.
+// Ranking chains per warp (counter tables, each over a contiguous group of the
+// warp's rows): one; splitting the rows into two interleaved chains measured
+// slower.
+__host__ __device__ constexpr int scatter_chains(int) { return 1; }
 __host__ __device__ constexpr int scatter_union_words(int nb) {
-  return (kScatThreads / 32) * nb / 2 > 2 * kBinChunk ? (kScatThreads / 32) * nb / 2
-                                                      : 2 * kBinChunk;
+  return (kScatThreads / 32) * scatter_chains(nb) * nb / 2 > 2 * kBinChunk
+             ? (kScatThreads / 32) * scatter_chains(nb) * nb / 2
+             : 2 * kBinChunk;
 }
 __host__ __device__ constexpr int scatter_smem_bytes(int nb) {
   return (scatter_union_words(nb) + 2 * nb + kBinChunk) * 4;
@@ -255,9 +274,12 @@ __global__ void __launch_bounds__(kScatThreads, 2) k_scatter(
     int shift) {
   constexpr int kWarps = kScatThreads / 32;
   constexpr int nb = 1 << BITS;
+  constexpr int kCh = scatter_chains(nb);            // counter tables per warp
+  constexpr int kVW = kWarps * kCh;                   // virtual warps, in input order
+  constexpr int kRows = kScatItems / kCh;             // rows per chain
   constexpr uint32_t mask = (uint32_t)(nb - 1);
   extern __shared__ uint32_t sm[];
-  uint16_t *cnt = reinterpret_cast<uint16_t *>(sm);  // [kWarps][nb], then chunk positions
+  uint16_t *cnt = reinterpret_cast<uint16_t *>(sm);  // [kVW][nb], then chunk positions
   uint32_t *sk = sm;                                  // [kBinChunk] staged keys
   uint32_t *sv = sm + kBinChunk;                      // [kBinChunk] staged values
   uint32_t *lst = sm + scatter_union_words(nb);       // [nb] start of each digit in the chunk
@@ -279,7 +301,7 @@ __global__ void __launch_bounds__(kScatThreads, 2) k_scatter(
   }
   const int64_t ncells = (int64_t)nb * nchunks;
   const uint32_t total = *n_total;
-  for (int i = threadIdx.x; i < kWarps * nb / 2; i += kScatThreads) sm[i] = 0;
+  for (int i = threadIdx.x; i < kVW * nb / 2; i += kScatThreads) sm[i] = 0;
   for (int d = threadIdx.x; d < nb; d += kScatThreads) {
     const int64_t cell = (int64_t)d * nchunks + chunk;
     const uint32_t b = hscan[cell];
@@ -291,7 +313,7 @@ __global__ void __launch_bounds__(kScatThreads, 2) k_scatter(
   for (int d = threadIdx.x; d < nb; d += kScatThreads) gofs[d] -= lst[d];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1;
-  uint16_t *my = cnt + warp * nb;
+  uint16_t *my = cnt + warp * kCh * nb;  // chain h of this warp: my + h * nb
   const int wloc = warp * (32 * kScatItems) + lane;  // local index of row 0
   // ps: two 16-bit ranks (then chunk positions, < 8192) per register
   uint32_t kk[kScatItems], ps[kScatItems / 2], ok = 0;
@@ -304,33 +326,38 @@ __global__ void __launch_bounds__(kScatThreads, 2) k_scatter(
     ok |= kept ? (1u << i) : 0u;
   }
 #pragma unroll
-  for (int i = 0; i < kScatItems; ++i) {
-    const bool kept = (ok >> i) & 1u;
-    const uint32_t d = (kk[i] >> shift) & mask;
-    // lanes with the same digit (kept ones) or the other dropped lanes
-    uint32_t peers = __ballot_sync(0xffffffffu, kept);
-    if (!kept) peers = ~peers;
+  for (int j = 0; j < kRows; ++j) {
 #pragma unroll
-    for (int b = 0; b < BITS; ++b) {
-      const uint32_t bit = (d >> b) & 1u;
-      const uint32_t bm = __ballot_sync(0xffffffffu, bit);
-      peers &= bm ^ (bit - 1u);  // bm where the bit is set, ~bm where it is not
+    for (int h = 0; h < kCh; ++h) {
+      const int i = h * kRows + j;  // row i of the warp, chain h
+      const bool kept = (ok >> i) & 1u;
+      const uint32_t d = (kk[i] >> shift) & mask;
+      // lanes with the same digit (kept ones) or the other dropped lanes
+      uint32_t peers = __ballot_sync(0xffffffffu, kept);
+      if (!kept) peers = ~peers;
+#pragma unroll
+      for (int b = 0; b < BITS; ++b) {
+        const uint32_t bit = (d >> b) & 1u;
+        const uint32_t bm = __ballot_sync(0xffffffffu, bit);
+        peers &= bm ^ (bit - 1u);  // bm where the bit is set, ~bm where it is not
+      }
+      const uint32_t before = __popc(peers & lt);
+      uint16_t *myh = my + h * nb;
+      uint32_t c = 0;
+      if (kept) c = myh[d];
+      __syncwarp();
+      if (kept && before == 0) myh[d] = (uint16_t)(c + __popc(peers));
+      __syncwarp();
+      const uint32_t r = c + before;
+      ps[i / 2] = (i & 1) ? (ps[i / 2] | (r << 16)) : r;
     }
-    const uint32_t before = __popc(peers & lt);
-    uint32_t c = 0;
-    if (kept) c = my[d];
-    __syncwarp();
-    if (kept && before == 0) my[d] = (uint16_t)(c + __popc(peers));
-    __syncwarp();
-    const uint32_t r = c + before;
-    ps[i / 2] = (i & 1) ? (ps[i / 2] | (r << 16)) : r;
   }
   __syncthreads();
   // counters -> chunk positions: start of the digit plus the earlier warps' counts
   for (int d = threadIdx.x; d < nb; d += kScatThreads) {
     uint32_t run = lst[d];
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) {
+    for (int w = 0; w < kVW; ++w) {
       const uint32_t v = cnt[w * nb + d];
       cnt[w * nb + d] = (uint16_t)run;
       run += v;
@@ -339,7 +366,8 @@ __global__ void __launch_bounds__(kScatThreads, 2) k_scatter(
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < kScatItems; ++i)
-    if ((ok >> i) & 1u) ps[i / 2] += (uint32_t)my[(kk[i] >> shift) & mask] << (16 * (i & 1));
+    if ((ok >> i) & 1u)
+      ps[i / 2] += (uint32_t)my[(i / kRows) * nb + ((kk[i] >> shift) & mask)] << (16 * (i & 1));
   cp_async_wait_all();
   __syncthreads();  // counters read, values arrived
 #pragma unroll
@@ -363,17 +391,35 @@ __global__ void __launch_bounds__(kScatThreads, 2) k_scatter(
 }
 
 // Segment bounds of the sorted keys: seg_lo[k] = first index, seg_hi[k] = one
-// past the last index of key k (both 0 for absent keys).
+// past the last index of key k (both 0 for absent keys). Each thread takes 8
+// consecutive keys (two 16-byte loads) and the keys on either side of them.
 // Keys at or beyond npx (impossible for a correct sort) are not written.
 __global__ void k_seg(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ n_dev,
                       uint32_t *__restrict__ seg_lo, uint32_t *__restrict__ seg_hi, int64_t npx) {
   const int64_t n = *n_dev;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    uint32_t k = keys[i];
-    if ((int64_t)k >= npx) continue;
-    if (i == 0 || keys[i - 1] != k) seg_lo[k] = (uint32_t)i;
-    if (i == n - 1 || keys[i + 1] != k) seg_hi[k] = (uint32_t)(i + 1);
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; 8 * g < n;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i0 = 8 * g;
+    uint32_t k[10];  // k[0] = keys[i0 - 1], k[1..8] = keys[i0 .. i0 + 7], k[9] = keys[i0 + 8]
+    if (i0 + 8 <= n) {
+      const uint4 a = *reinterpret_cast<const uint4 *>(keys + i0);
+      const uint4 b = *reinterpret_cast<const uint4 *>(keys + i0 + 4);
+      k[1] = a.x; k[2] = a.y; k[3] = a.z; k[4] = a.w;
+      k[5] = b.x; k[6] = b.y; k[7] = b.z; k[8] = b.w;
+    } else {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) k[1 + u] = i0 + u < n ? keys[i0 + u] : 0xffffffffu;
+    }
+    k[0] = i0 > 0 ? keys[i0 - 1] : 0xffffffffu;
+    k[9] = i0 + 8 < n ? keys[i0 + 8] : 0xffffffffu;
+#pragma unroll
+    for (int u = 1; u <= 8; ++u) {
+      const int64_t i = i0 + u - 1;
+      const uint32_t kk = k[u];
+      if (i >= n || (int64_t)kk >= npx) continue;
+      if (i == 0 || k[u - 1] != kk) seg_lo[kk] = (uint32_t)i;
+      if (i == n - 1 || k[u + 1] != kk) seg_hi[kk] = (uint32_t)(i + 1);
+    }
   }
 }
 
@@ -494,12 +540,64 @@ __global__ void k_scan_add(T *out, const T *part, int64_t n) {
     if (t0 + i < n) out[t0 + i] += add;
 }
 
-// Recursive exclusive scan; scratch holds the per-level partials and, when
-// total is not null, the grand total is written there.
+// Sum of each tile of in[] into part[tile].
+template <typename T>
+__global__ void __launch_bounds__(kScanThreads) k_tile_sum(const T *in, T *part, int64_t n) {
+  __shared__ T ws[33];
+  const int64_t t0 = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  T v = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) v += (t0 + i < n) ? in[t0 + i] : T(0);
+  T total;
+  block_exclusive_scan<T>(v, ws, total);
+  if (threadIdx.x == 0) part[blockIdx.x] = total;
+}
+
+// Exclusive scan of each tile offset by the sum of the tiles before it (summed
+// by the block itself from part[]); the last tile writes the grand total.
+// In place is allowed.
+template <typename T>
+__global__ void __launch_bounds__(kScanThreads) k_scan_prefixed(const T *in, T *out,
+                                                                const T *part, int64_t n,
+                                                                T *total_out) {
+  __shared__ T ws[33];
+  T pre = 0;
+  for (int64_t j = threadIdx.x; j < (int64_t)blockIdx.x; j += kScanThreads) pre += part[j];
+  T pre_total;
+  block_exclusive_scan<T>(pre, ws, pre_total);
+  __syncthreads();  // ws is reused below
+  const int64_t t0 = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  T v[kScanItems];
+  T sum = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    v[i] = (t0 + i < n) ? in[t0 + i] : T(0);
+    sum += v[i];
+  }
+  T tile_total;
+  T ex = block_exclusive_scan<T>(sum, ws, tile_total) + pre_total;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    if (t0 + i < n) out[t0 + i] = ex;
+    ex += v[i];
+  }
+  if (total_out && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0)
+    *total_out = pre_total + tile_total;
+}
+
+// Exclusive scan; up to kScanDirectTiles tiles by a tile-sum pass and one
+// prefixed scan pass, beyond that recursively (scratch holds the per-level
+// partials). When total is not null, the grand total is written there.
+constexpr int64_t kScanDirectTiles = 4096;
 template <typename T>
 cudaError_t scan_rec(const T *in, T *out, int64_t n, T *scratch, T *total, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   int64_t nt = ceil_div(n, kScanTile);
+  if (nt > 1 && nt <= kScanDirectTiles) {
+    k_tile_sum<T><<<(unsigned)nt, kScanThreads, 0, s>>>(in, scratch, n);
+    k_scan_prefixed<T><<<(unsigned)nt, kScanThreads, 0, s>>>(in, out, scratch, n, total);
+    return cudaGetLastError();
+  }
   k_scan_tile<T><<<(unsigned)nt, kScanThreads, 0, s>>>(in, out, nt > 1 ? scratch : total, n);
   if (nt > 1) {
     cudaError_t e = scan_rec<T>(scratch, scratch, nt, scratch + nt, total, s);

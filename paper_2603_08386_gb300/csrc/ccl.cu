@@ -356,6 +356,78 @@ ddhf_status launch_label(Ctx *c, const uint8_t *mask, int32_t *labels, uint64_t 
   return DDHF_OK;
 }
 
+// Dominant frequency of each box: block b scans the rows of box b; warp by
+// warp, a row's active pixels are the run of the (ascending) active list
+// between the keys y W + x0 and y W + x1, found by binary search, and each
+// rotor pixel offers (SNR bits, -active index) to a maximum; the winner's
+// dominant bin and SNR are written (-1 and 0 when the box holds no rotor
+// pixel).
+__global__ void __launch_bounds__(256) k_box_f0(const uint32_t *__restrict__ active,
+                                                const uint64_t *__restrict__ counters,
+                                                const uint8_t *__restrict__ mask,
+                                                const float *__restrict__ snr,
+                                                const int32_t *__restrict__ f0,
+                                                const ddhf_box *__restrict__ boxes,
+                                                const int32_t *__restrict__ n_boxes, int32_t cap,
+                                                int W, int H, int32_t *f0_out, float *snr_out) {
+  __shared__ unsigned long long red[8];
+  const int b = blockIdx.x;
+  const int nb = min(*n_boxes, cap);
+  if (b >= nb) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t n_act = (int64_t)counters[2];
+  const ddhf_box bx = boxes[b];
+  const int x0 = max(bx.x0, 0), x1 = min(bx.x1, W - 1);
+  const int y0 = max(bx.y0, 0), y1 = min(bx.y1, H - 1);
+  unsigned long long best = 0ull;
+  for (int y = y0 + warp; y <= y1 && x0 <= x1; y += 8) {
+    const uint32_t lo = (uint32_t)((int64_t)y * W + x0), hi = (uint32_t)((int64_t)y * W + x1);
+    // first index with active[i] >= lo
+    int64_t l = 0, r = n_act;
+    while (l < r) {
+      const int64_t m = (l + r) >> 1;
+      if (active[m] < lo) l = m + 1;
+      else r = m;
+    }
+    for (int64_t i = l + lane;; i += 32) {
+      const bool in = i < n_act && active[i] <= hi;
+      if (in && mask[active[i]]) {
+        const unsigned long long v =
+            ((unsigned long long)__float_as_uint(snr[i]) << 32) | (0xffffffffu - (uint32_t)i);
+        best = v > best ? v : best;
+      }
+      if (!__any_sync(0xffffffffu, in)) break;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long u = __shfl_xor_sync(0xffffffffu, best, o);
+    best = u > best ? u : best;
+  }
+  if (lane == 0) red[warp] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < 8; ++w) best = red[w] > best ? red[w] : best;
+    if (best == 0ull) {
+      f0_out[b] = -1;
+      if (snr_out) snr_out[b] = 0.f;
+    } else {
+      const uint32_t i = 0xffffffffu - (uint32_t)best;
+      f0_out[b] = f0[i];
+      if (snr_out) snr_out[b] = snr[i];
+    }
+  }
+}
+
+ddhf_status launch_box_f0(Ctx *c, int slot, const ddhf_box *boxes, const int32_t *n_boxes,
+                          int32_t cap, int32_t *f0_out, float *snr_out, cudaStream_t s) {
+  const Slot &sl = c->slots[slot];
+  if (cap > 0)
+    k_box_f0<<<cap, 256, 0, s>>>(sl.active, sl.counters, sl.mask, sl.snr, sl.f0, boxes, n_boxes,
+                                 cap, c->W, c->H, f0_out, snr_out);
+  DDHF_CUDA_TRY(c, cudaGetLastError());
+  return DDHF_OK;
+}
+
 ddhf_status launch_components(Ctx *c, const int32_t *labels, int32_t row0, ddhf_component *out,
                               int32_t cap, int32_t *n_out, cudaStream_t s) {
   const int blocks = c->num_sms * 8;

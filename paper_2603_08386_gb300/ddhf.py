@@ -135,6 +135,7 @@ SIGNATURES = {
     "ddhf_slide_get_stats": (_I32, [_VP, ctypes.POINTER(ddhf_slide_stats)]),
     "ddhf_measure_pipes": (_I32, [ctypes.POINTER(ddhf_pipe_peaks), _I32, _VP]),
     "ddhf_export_labels": (_I32, [_VP, _I32, _VP, _VP]),
+    "ddhf_box_frequencies": (_I32, [_VP, _I32, _VP, _VP, _I32, _VP, _VP, _VP]),
     "ddhf_debug_fail_alloc_after": (_I32, [_I32]),
 }
 
@@ -358,6 +359,12 @@ def ddhf_debug_fail_alloc_after(n):
 
 def ddhf_export_labels(ctx, slot, labels, stream=None):
     _check(load().ddhf_export_labels(ctx, int(slot), _ptr(labels), _stream(stream)), ctx)
+
+
+def ddhf_box_frequencies(ctx, slot, boxes, n_boxes, cap, f0_bin, snr=None, stream=None):
+    """Dominant bin (and SNR) of each detected box: its strongest rotor pixel."""
+    _check(load().ddhf_box_frequencies(ctx, int(slot), _ptr(boxes), _ptr(n_boxes), int(cap),
+                                       _ptr(f0_bin), _ptr(snr), _stream(stream)), ctx)
 
 
 def ddhf_enable_stage_timing(ctx, enable=True):
@@ -611,3 +618,27 @@ def events_to_device(scene, device="cuda"):
     """Upload a synthetic Scene's event arrays to device tensors."""
     return (torch.from_numpy(scene.x).to(device), torch.from_numpy(scene.y).to(device),
             torch.from_numpy(scene.t).to(device), torch.from_numpy(scene.p).to(device))
+
+
+def stack_windows(windows, H):
+    """Lay several windows of one H-row sensor out as one window of a sensor
+    len(windows) times as tall, so that one binning and one call (for
+    instance one ddhf_softcomb over the whole batch) cover them all.
+
+    windows: sequence of (x, y, t, p, t0) numpy arrays / ints, all of the same
+    window length. Window b's rows go to y + b H and its times to t - t0_b, so
+    every event keeps its offset tau = t - t0 in the stacked window (t0 = 0);
+    a pixel's events, their order and their tau are those of its own window,
+    so per-pixel results equal the per-window ones bit for bit. Returns
+    (x, y, t, p) numpy arrays; the stacked sensor is W x (len(windows) H) and
+    pixel key y*W + x of window b is key_b + b*H*W."""
+    import numpy as np
+    if len(windows) * H > 32767:
+        raise ValueError("stacked sensor taller than int16 rows allow")
+    xs, ys, ts, ps = [], [], [], []
+    for b, (x, y, t, p, t0) in enumerate(windows):
+        xs.append(np.asarray(x, np.int16))
+        ys.append((np.asarray(y, np.int32) + b * H).astype(np.int16))
+        ts.append(np.asarray(t, np.int64) - np.int64(t0))
+        ps.append(np.asarray(p, np.int8))
+    return np.concatenate(xs), np.concatenate(ys), np.concatenate(ts), np.concatenate(ps)

@@ -11,7 +11,8 @@ statistics are further from the thresholds than the arithmetic (1e-5) and
 the FP32 spectrum can move them (oracle_margins states the bounds).
 Boxes are compared without condition: always against the oracle's labelling
 and Eq. 12 merging of the GPU's own mask, and against the oracle's boxes when
-no pixel is inside its margin. The batched, graph-replayed call with the
+no pixel is inside its margin; each box's dominant frequency (its strongest
+rotor pixel) against the oracle's selection on the GPU's own scores. The batched, graph-replayed call with the
 benchmark's tuning (8 warps per block, overlapped windows, hybrid spectra for
 pixels of at least 128 events) must give the same bits as one call per window.
 """
@@ -54,6 +55,9 @@ def test_labelled_detection_matches_oracle(seed, prm):
     c.set_tuning(**BENCH_TUNING)
     bx, nb, mask = c.detect(*ev, s.t0, s.window_us, cap=256, want_mask=True)
     sc = c.scores()
+    f0b = torch.full((256,), -7, dtype=torch.int32, device="cuda")
+    snrb = torch.zeros(256, device="cuda")
+    ddhf.ddhf_box_frequencies(c.h, 0, bx, nb, 256, f0b, snrb)
     P32 = c.power_spectrum("hybrid").cpu().numpy()  # the spectra the detection scored
     st = c.stats()
     c.close()
@@ -66,6 +70,12 @@ def test_labelled_detection_matches_oracle(seed, prm):
     # boxes are exactly the oracle's segmentation of the GPU's own mask
     ref_own = oracle_margins.segment(gmask, s.W, s.H, prm["A_min"], prm["alpha"], cap=256)
     np.testing.assert_array_equal(bx[:n].cpu().numpy(), ref_own)
+    # each box's dominant bin: its strongest rotor pixel (Eq. 11 per pixel)
+    rf, rs = oracle.box_frequencies(bx[:n].cpu().numpy(), act, gmask, sc["snr"].cpu().numpy(),
+                                    sc["f0_bin"].cpu().numpy(), s.W)
+    np.testing.assert_array_equal(f0b[:n].cpu().numpy(), rf)
+    np.testing.assert_array_equal(snrb[:n].cpu().numpy().view(np.int32), rs.view(np.int32))
+    assert (rf >= 0).all() and (f0b[n:].cpu().numpy() == -7).all()
     # rotor bits against the FP64 oracle outside the margins
     b = oracle.bin_events(s.W, s.H, s.x, s.y, s.t, s.p, s.t0, s.window_us)
     np.testing.assert_array_equal(np.flatnonzero(b["counts"] >= prm["n_min"]), act)

@@ -170,3 +170,53 @@ def test_spectrum_median_exact(setup):
             ref = ((srt[:, N // 2 - 1] + srt[:, N // 2]) * np.float32(0.5)).astype(np.float32)
         np.testing.assert_array_equal(med.cpu().numpy(), ref)
         c.close()
+
+
+def test_stacked_batch_equals_single_windows(setup):
+    # three windows laid out as one window of a sensor three times as tall
+    # (ddhf.stack_windows, the C4 batch layout): one binning and one
+    # ddhf_softcomb call per direction give every pixel the S and dS/df0 of its
+    # own window's call, bit for bit
+    scenes = [synth.small_scene(80 + b, W=48, H=40, n_noise=8_000, drone_px=60, f0_hz=150.0,
+                                window_us=40_000, grid=synth.hz_grid(0, 2, 750)) for b in range(3)]
+    W, H, grid, win = 48, 40, scenes[0].grid, scenes[0].window_us
+    Q, delta, n_h = 3, 2.0, 6
+    w = torch.linspace(0.5, 1.5, n_h, device="cuda")
+    sg = torch.linspace(1.0, 3.0, n_h, device="cuda")
+    per_S, per_g, per_keys = [], [], []
+    for b, s in enumerate(scenes):
+        c = ddhf.Context(W, H, grid, max_events=s.n)
+        c.bin_events(*ddhf.events_to_device(s), s.t0, win)
+        pix = c.csr()["active"].clone()
+        keys = pix.long() + b * H * W
+        f0 = 140.0 + (keys % 97).float().cuda() * 0.2
+        B = 1.0 + (keys % 13).float().cuda()
+        S = torch.empty(pix.numel(), device="cuda")
+        ddhf.ddhf_softcomb(c.h, pix, f0, n_h, Q, delta, win / 2, w, sg, B, S=S)
+        gf0 = torch.empty(pix.numel(), device="cuda")
+        gw, gs = torch.empty(n_h, device="cuda"), torch.empty(n_h, device="cuda")
+        ddhf.ddhf_softcomb(c.h, pix, f0, n_h, Q, delta, win / 2, w, sg, B,
+                           grad_S=torch.ones_like(S), grad_f0=gf0, grad_w=gw, grad_sigma=gs)
+        per_S.append(S)
+        per_g.append(gf0)
+        per_keys.append(keys)
+        c.stats()
+        c.close()
+    xs, ys, ts, ps = ddhf.stack_windows([(s.x, s.y, s.t, s.p, s.t0) for s in scenes], H)
+    cs = ddhf.Context(W, 3 * H, grid, max_events=xs.size)
+    cs.bin_events(*(torch.from_numpy(a).cuda() for a in (xs, ys, ts, ps)), 0, win)
+    pix = cs.csr()["active"].clone()
+    keys = pix.long()
+    assert torch.equal(keys, torch.cat(per_keys))
+    f0 = 140.0 + (keys % 97).float().cuda() * 0.2
+    B = 1.0 + (keys % 13).float().cuda()
+    S = torch.empty(pix.numel(), device="cuda")
+    ddhf.ddhf_softcomb(cs.h, pix, f0, n_h, Q, delta, win / 2, w, sg, B, S=S)
+    gf0 = torch.empty(pix.numel(), device="cuda")
+    gw, gs = torch.empty(n_h, device="cuda"), torch.empty(n_h, device="cuda")
+    ddhf.ddhf_softcomb(cs.h, pix, f0, n_h, Q, delta, win / 2, w, sg, B,
+                       grad_S=torch.ones_like(S), grad_f0=gf0, grad_w=gw, grad_sigma=gs)
+    cs.stats()
+    cs.close()
+    assert torch.equal(S.view(torch.int32), torch.cat(per_S).view(torch.int32))
+    assert torch.equal(gf0.view(torch.int32), torch.cat(per_g).view(torch.int32))

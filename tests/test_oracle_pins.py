@@ -473,3 +473,22 @@ def test_ndft_at_negative_frequency_is_conjugate():
     Fm, Dm = oracle.ndft_at(tau, pol, -f)
     np.testing.assert_allclose(Fm, np.conj(Fp), atol=1e-9)
     np.testing.assert_allclose(Dm, -np.conj(Dp), atol=1e-6)  # D(-f) = -conj(D(f))
+
+
+def test_box_frequencies_hand_case():
+    # 5x4 sensor; rotor pixels (x, y): (1,1) snr 3 bin 7, (3,1) snr 5 bin 9,
+    # (2,2) snr 5 bin 4 (ties with (3,1): key 8 < 12 wins in a box holding both),
+    # (4,3) snr 9 bin 2 but masked off; a box with no rotor pixel gives -1
+    W = 5
+    active = np.array([6, 8, 12, 19], np.int64)          # (1,1), (3,1), (2,2), (4,3)
+    mask = np.zeros(20, np.uint8)
+    mask[[6, 8, 12]] = 1
+    snr = np.array([3.0, 5.0, 5.0, 9.0], np.float32)
+    f0 = np.array([7, 9, 4, 2], np.int32)
+    boxes = np.array([[0, 0, 4, 3, 0],    # everything: tie 5.0 at keys 8 and 12 -> key 8
+                      [0, 0, 1, 1, 0],    # only (1,1)
+                      [2, 2, 4, 3, 0],    # (2,2) rotor, (4,3) not
+                      [0, 3, 3, 3, 0]])   # no rotor pixel
+    fb, sb = oracle.box_frequencies(boxes, active, mask, snr, f0, W)
+    np.testing.assert_array_equal(fb, [9, 7, 4, -1])
+    np.testing.assert_array_equal(sb, np.float32([5.0, 3.0, 5.0, 0.0]))
