@@ -682,8 +682,14 @@ def main():
         base = {k: v for k, v in tuning.items() if k != "how"}
         forms = dict(window="stream 0, window 0", active_pixels=na0,
                      terms=terms_of(w0, W, H, nb))
-        for name, form, tun in (("blocked", ddhf.FORM["blocked"], dict(base, hybrid_min=0)),
-                                ("hybrid", ddhf.FORM["hybrid"], dict(base, hybrid_min=hm))):
+        # the blocked kernel alone takes every pixel, so its own heavy threshold
+        # (block-per-pixel from heavy_min events) is chosen here among three
+        # values; the step's tuning picks heavy_min for the pixels that the
+        # hybrid route leaves to it
+        runs = [("blocked", ddhf.FORM["blocked"], dict(base, hybrid_min=0, heavy_min=h))
+                for h in sorted({256, 1024, int(base.get("heavy_min", 1024))})]
+        runs.append(("hybrid", ddhf.FORM["hybrid"], dict(base, hybrid_min=hm)))
+        for name, form, tun in runs:
             fc.set_tuning(**tun)
             for _ in range(3):
                 ddhf.ddhf_power_spectrum(fc.h, form, P0, na0)
@@ -695,7 +701,13 @@ def main():
                 ddhf.ddhf_power_spectrum(fc.h, form, P0, na0)
                 b_.record()
             torch.cuda.synchronize()
-            forms[name + "_ms"] = float(np.median([a_.elapsed_time(b_) for a_, b_ in fe]))
+            ms_ = float(np.median([a_.elapsed_time(b_) for a_, b_ in fe]))
+            if name == "hybrid":
+                forms["hybrid_ms"] = ms_
+            else:
+                forms.setdefault("blocked_by_heavy_min", {})[str(tun["heavy_min"])] = ms_
+                if ms_ < forms.get("blocked_ms", float("inf")):
+                    forms["blocked_ms"], forms["blocked_heavy_min"] = ms_, tun["heavy_min"]
         fc.stats()
         fc.close()
         cnt0 = _counts(w0, W, H)

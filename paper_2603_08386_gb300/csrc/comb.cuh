@@ -955,11 +955,8 @@ __device__ __forceinline__ CombOut comb_warp_fast_smem(const float *Pw, const Co
   bool bad = false;
 
   // ---- Eq. 7 sums (fixed order: 4-bin groups lane-strided, the (at most 3)
-  // tail bins in the lane owning group N / 4, then a butterfly) and the
-  // histogram
-#pragma unroll
-  for (int q = 0; q < CombFast::kHistBytes / 512; ++q)
-    reinterpret_cast<uint4 *>(hist)[q * 32 + lane] = make_uint4(0u, 0u, 0u, 0u);
+  // tail bins in the lane owning group N / 4, then a butterfly); the
+  // histogram only for a pixel that passes the flatness test
   const int nfull = N >> 2;
   const int tail_lane = nfull & 31;
   const int jt = nfull << 2;
@@ -982,23 +979,27 @@ __device__ __forceinline__ CombOut comb_warp_fast_smem(const float *Pw, const Co
     sl2 = __fadd_rn(sl2, lg2_normal(fmaxf(v.y, 1e-30f)));
     sl2 = __fadd_rn(sl2, lg2_normal(fmaxf(v.z, 1e-30f)));
     sl2 = __fadd_rn(sl2, lg2_normal(fmaxf(v.w, 1e-30f)));
-    hist_add(hist_sa, bucket_bits(v.x, scale));
-    hist_add(hist_sa, bucket_bits(v.y, scale));
-    hist_add(hist_sa, bucket_bits(v.z, scale));
-    hist_add(hist_sa, bucket_bits(v.w, scale));
   }
-  if (lane == tail_lane) {
-    for (int j = jt; j < N; ++j) {
-      const float v = Pw[j];
-      sl2 = __fadd_rn(sl2, lg2_normal(fmaxf(v, 1e-30f)));
-      hist_add(hist_sa, bucket_bits(v, scale));
-    }
-  }
+  if (lane == tail_lane)
+    for (int j = jt; j < N; ++j) sl2 = __fadd_rn(sl2, lg2_normal(fmaxf(Pw[j], 1e-30f)));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) sl2 = __fadd_rn(sl2, __shfl_xor_sync(0xffffffffu, sl2, o));
   const float slog = __fmul_rn(sl2, 0.693147180559945309f);
   out.log_sf = sum > 0.f ? __fsub_rn(__fdiv_rn(slog, fN), __logf(__fdiv_rn(sum, fN))) : 0.f;
   if (!(out.log_sf <= cc.ln_tau_sf) || cc.w_hi < cc.w_lo) return out;
+#pragma unroll
+  for (int q = 0; q < CombFast::kHistBytes / 512; ++q)
+    reinterpret_cast<uint4 *>(hist)[q * 32 + lane] = make_uint4(0u, 0u, 0u, 0u);
+  __syncwarp();
+  for (int q = lane; q < nfull; q += 32) {
+    const float4 v = P4[q];
+    hist_add(hist_sa, bucket_bits(v.x, scale));
+    hist_add(hist_sa, bucket_bits(v.y, scale));
+    hist_add(hist_sa, bucket_bits(v.z, scale));
+    hist_add(hist_sa, bucket_bits(v.w, scale));
+  }
+  if (lane == tail_lane)
+    for (int j = jt; j < N; ++j) hist_add(hist_sa, bucket_bits(Pw[j], scale));
   __syncwarp();
 
   // ---- the band: lane p < bw holds the bin at full rank lo_r + p
@@ -1132,9 +1133,6 @@ __device__ __forceinline__ CombOut comb_warp_fast_regs(const float *Pw, const Co
   out.rotor = 0;
   out.bad = 0;
   bool bad = false;
-#pragma unroll
-  for (int q = 0; q < CombFast::kHistBytes / 512; ++q)
-    reinterpret_cast<uint4 *>(hist)[q * 32 + lane] = make_uint4(0u, 0u, 0u, 0u);
   // ---- the lane's 24 bins
   const int base = kB * lane;
   const int nval = min(max(N - base, 0), kB);  // bins of this lane below N
@@ -1159,7 +1157,7 @@ __device__ __forceinline__ CombOut comb_warp_fast_regs(const float *Pw, const Co
       v[4 * k + 3] = t.w;
     }
   }
-  // ---- Eq. 7 sums and the histogram
+  // ---- Eq. 7 sums; the histogram only for a pixel that passes the flatness test
   float sum = 0.f;
 #pragma unroll
   for (int i = 0; i < kB; ++i) sum = __fadd_rn(sum, v[i]);
@@ -1171,21 +1169,22 @@ __device__ __forceinline__ CombOut comb_warp_fast_regs(const float *Pw, const Co
   __syncwarp();
   float sl2 = 0.f;
 #pragma unroll
-  for (int i = 0; i < kB; ++i) {
-    sl2 = __fadd_rn(sl2, lg2_normal(fmaxf(v[i], 1e-30f)));
-    hist_add(hist_sa, bucket_bits(v[i], scale));
-  }
+  for (int i = 0; i < kB; ++i) sl2 = __fadd_rn(sl2, lg2_normal(fmaxf(v[i], 1e-30f)));
   const int npad = kB - nval;
-  if (npad > 0) {
-    sl2 = __fmaf_rn(-(float)npad, lg2_normal(1e-30f), sl2);
-    atomicSub(&hist[0], (uint32_t)npad);  // bucket 0 is the low half of word 0
-  }
+  if (npad > 0) sl2 = __fmaf_rn(-(float)npad, lg2_normal(1e-30f), sl2);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) sl2 = __fadd_rn(sl2, __shfl_xor_sync(0xffffffffu, sl2, o));
   const float slog = __fmul_rn(sl2, 0.693147180559945309f);
   out.log_sf = sum > 0.f ? __fsub_rn(__fmul_rn(slog, cc.inv_N), __logf(__fmul_rn(sum, cc.inv_N)))
                          : 0.f;
   if (!(out.log_sf <= cc.ln_tau_sf) || cc.w_hi < cc.w_lo) return out;
+#pragma unroll
+  for (int q = 0; q < CombFast::kHistBytes / 512; ++q)
+    reinterpret_cast<uint4 *>(hist)[q * 32 + lane] = make_uint4(0u, 0u, 0u, 0u);
+  __syncwarp();
+#pragma unroll
+  for (int i = 0; i < kB; ++i) hist_add(hist_sa, bucket_bits(v[i], scale));
+  if (npad > 0) atomicSub(&hist[0], (uint32_t)npad);  // bucket 0 is the low half of word 0
   __syncwarp();
 
   // ---- window maxima of the lane's centres from its bins and three bins of
