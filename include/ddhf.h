@@ -120,6 +120,9 @@ typedef struct {
 #define DDHF_FLAG_CAPACITY 1u /* a caller-sized output overflowed */
 #define DDHF_FLAG_TIMEOUT 2u  /* a bounded device-side loop hit its limit */
 #define DDHF_FLAG_INTERNAL 4u /* an internal consistency check failed (reported as DDHF_ERR_CUDA) */
+#define DDHF_FLAG_INPUT 8u    /* a caller's device array held an out-of-range index (a pixel key
+                                 or label at or beyond W*H), skipped; reported as
+                                 DDHF_ERR_INVALID_ARG */
 
 /* NDFT evaluation forms for ddhf_power_spectrum (Eq. 6; all give P_j in FP32).
  *  SINCOS   one warp per pixel, lanes own bins; exact integer phase per term,
@@ -225,6 +228,16 @@ ddhf_status ddhf_hybrid_geometry(const ddhf_grid *grid, int64_t window_us, int32
  * every allocation it made released. Process-wide; not for concurrent use
  * with other contexts being created. */
 ddhf_status ddhf_debug_fail_alloc_after(int32_t n);
+
+/* Guard bytes: every workspace buffer of ddhf_create has 256 bytes of a fixed
+ * pattern before it and at least 256 after it (inside the same allocation),
+ * checked on the device by ddhf_get_stats, which reports a changed byte as
+ * DDHF_FLAG_INTERNAL (DDHF_ERR_CUDA): a kernel wrote outside its buffer.
+ * Test hook, not in the paper: overwrite one byte of the guard after
+ * workspace buffer `index` (in allocation order), so that the next
+ * ddhf_get_stats must report it. The byte lies inside the allocation. Returns
+ * DDHF_ERR_INVALID_ARG for an index beyond the buffers. */
+ddhf_status ddhf_debug_corrupt_guard(ddhf_ctx *ctx, int32_t index);
 
 /* Table 2 final values. out: host pointer. */
 ddhf_status ddhf_default_params(ddhf_params *out);

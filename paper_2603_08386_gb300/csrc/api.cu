@@ -41,13 +41,70 @@ ddhf_status dev_alloc(Ctx *c, T **p, size_t count) {
     c->last_error = "cudaMalloc: out of memory (injected failure)";
     return DDHF_ERR_CUDA;
   }
-  cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+  // [kCanaryBytes guard][buffer, rounded up to 256 bytes][kCanaryBytes guard]
+  const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  const size_t body = (bytes + 255) & ~(size_t)255;
+  cudaError_t e = cudaMalloc(&q, body + 2 * kCanaryBytes);
+  if (e == cudaSuccess) e = cudaMemset(q, kCanaryByte, kCanaryBytes);
+  unsigned char *user = static_cast<unsigned char *>(q) + kCanaryBytes;
+  if (e == cudaSuccess) e = cudaMemset(user + bytes, kCanaryByte, body - bytes + kCanaryBytes);
   if (e != cudaSuccess) {
+    if (q) cudaFree(q);
     c->last_error = std::string("cudaMalloc: ") + cudaGetErrorString(e);
     return DDHF_ERR_CUDA;
   }
-  *p = static_cast<T *>(q);
+  c->guarded.push_back(Ctx::Guarded{user, bytes});
+  *p = reinterpret_cast<T *>(user);
   return DDHF_OK;
+}
+
+// Free a workspace buffer: through its guard region when dev_alloc made it.
+void dev_free(Ctx *c, void *p) {
+  if (!p) return;
+  for (size_t i = 0; i < c->guarded.size(); ++i)
+    if (c->guarded[i].user == p) {
+      cudaFree(static_cast<unsigned char *>(p) - kCanaryBytes);
+      c->guarded[i] = c->guarded.back();
+      c->guarded.pop_back();
+      return;
+    }
+  cudaFree(p);
+}
+
+// Guard check: every byte of the regions listed must still be kCanaryByte.
+constexpr int kGuardBatch = 64;
+struct GuardList {
+  const unsigned char *p[kGuardBatch];
+  uint32_t len[kGuardBatch];
+  int n;
+};
+__global__ void k_check_guards(GuardList g, uint32_t *flags) {
+  const int r = blockIdx.x;
+  if (r >= g.n) return;
+  bool bad = false;
+  for (uint32_t i = threadIdx.x; i < g.len[r]; i += blockDim.x) bad |= g.p[r][i] != kCanaryByte;
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, DDHF_FLAG_INTERNAL);
+}
+
+// Launch the guard check over every guarded buffer (head and tail regions).
+cudaError_t check_guards(Ctx *c, cudaStream_t s) {
+  GuardList g{};
+  for (const Ctx::Guarded &b : c->guarded) {
+    const unsigned char *u = static_cast<const unsigned char *>(b.user);
+    const size_t body = (b.bytes + 255) & ~(size_t)255;
+    const unsigned char *regions[2] = {u - kCanaryBytes, u + b.bytes};
+    const size_t lens[2] = {kCanaryBytes, body - b.bytes + kCanaryBytes};
+    for (int k = 0; k < 2; ++k) {
+      g.p[g.n] = regions[k];
+      g.len[g.n] = (uint32_t)lens[k];
+      if (++g.n == kGuardBatch) {
+        k_check_guards<<<kGuardBatch, 128, 0, s>>>(g, c->flags);
+        g.n = 0;
+      }
+    }
+  }
+  if (g.n) k_check_guards<<<g.n, 128, 0, s>>>(g, c->flags);
+  return cudaGetLastError();
 }
 
 #define DDHF_TRY(x)                      \
@@ -59,9 +116,7 @@ ddhf_status dev_alloc(Ctx *c, T **p, size_t count) {
 void free_all(Ctx *c) {
   slide_free(c);
   hybrid_free(c);
-  auto F = [](void *p) {
-    if (p) cudaFree(p);
-  };
+  auto F = [c](void *p) { dev_free(c, p); };
   F(c->keysA);
   F(c->valsA);
   F(c->keysB);
@@ -339,6 +394,16 @@ const char *ddhf_status_string(ddhf_status s) {
     case DDHF_ERR_STATE: return "call out of order";
   }
   return "unknown status";
+}
+
+ddhf_status ddhf_debug_corrupt_guard(ddhf_ctx *h, int32_t index) {
+  if (!h) return DDHF_ERR_INVALID_ARG;
+  Ctx *c = &h->c;
+  if (index < 0 || index >= (int32_t)c->guarded.size())
+    return fail(c, DDHF_ERR_INVALID_ARG, "guard index out of range");
+  const Ctx::Guarded &b = c->guarded[index];
+  DDHF_CUDA_TRY(c, cudaMemset(static_cast<unsigned char *>(b.user) + b.bytes, 0, 1));
+  return DDHF_OK;
 }
 
 ddhf_status ddhf_debug_fail_alloc_after(int32_t n) {
@@ -922,6 +987,8 @@ ddhf_status ddhf_get_stats(ddhf_ctx *h, ddhf_stats *out) {
   if (!h || !out) return DDHF_ERR_INVALID_ARG;
   Ctx *c = &h->c;
   DDHF_CUDA_TRY(c, cudaStreamSynchronize(c->last_stream));
+  DDHF_CUDA_TRY(c, check_guards(c, c->last_stream));
+  DDHF_CUDA_TRY(c, cudaStreamSynchronize(c->last_stream));
   uint64_t cnt[8];
   uint32_t flags = 0;
   int32_t nbox = 0;
@@ -940,6 +1007,8 @@ ddhf_status ddhf_get_stats(ddhf_ctx *h, ddhf_stats *out) {
   out->device_flags = flags;
   if (flags) DDHF_CUDA_TRY(c, cudaMemset(c->flags, 0, sizeof(uint32_t)));
   if (flags & DDHF_FLAG_INTERNAL) return fail(c, DDHF_ERR_CUDA, "internal consistency check failed");
+  if (flags & DDHF_FLAG_INPUT)
+    return fail(c, DDHF_ERR_INVALID_ARG, "a device array held a pixel key or label out of range");
   if (flags & DDHF_FLAG_TIMEOUT) return fail(c, DDHF_ERR_TIMEOUT, "device-side loop limit reached");
   if (flags & DDHF_FLAG_CAPACITY) return fail(c, DDHF_ERR_CAPACITY, "output capacity exceeded");
   return DDHF_OK;

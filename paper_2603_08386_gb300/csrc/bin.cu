@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(kScatThreads, 2) k_scatter(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, int64_t n_in,
     const uint32_t *__restrict__ n_total, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, const uint32_t *__restrict__ hscan, int64_t nchunks,
-    int shift) {
+    int shift, uint32_t *flags) {
   constexpr int kWarps = kScatThreads / 32;
   constexpr int nb = 1 << BITS;
   constexpr int kCh = scatter_chains(nb);            // counter tables per warp
@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(kScatThreads, 2) k_scatter(
 #pragma unroll
   for (int i = 0; i < kScatItems; ++i) {
     const uint32_t pos = (ps[i / 2] >> (16 * (i & 1))) & 0xffffu;
-    if (((ok >> i) & 1u) && pos < (uint32_t)kBinChunk) {
+    if (((ok >> i) & 1u) && ddhf_check(pos < (uint32_t)kBinChunk, flags)) {
       sk[pos] = kk[i];
       sv[pos] = vbuf[wloc + 32 * i];
     }
@@ -386,6 +386,8 @@ __global__ void __launch_bounds__(kScatThreads, 2) k_scatter(
     if (dest < total) {  // always true when the counts agree with the table
       kout[dest] = key;
       vout[dest] = sv[sl];
+    } else {
+      ddhf_check(false, flags);
     }
   }
 }
@@ -395,7 +397,8 @@ __global__ void __launch_bounds__(kScatThreads, 2) k_scatter(
 // consecutive keys (two 16-byte loads) and the keys on either side of them.
 // Keys at or beyond npx (impossible for a correct sort) are not written.
 __global__ void k_seg(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ n_dev,
-                      uint32_t *__restrict__ seg_lo, uint32_t *__restrict__ seg_hi, int64_t npx) {
+                      uint32_t *__restrict__ seg_lo, uint32_t *__restrict__ seg_hi, int64_t npx,
+                      uint32_t *flags) {
   const int64_t n = *n_dev;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; 8 * g < n;
        g += (int64_t)gridDim.x * blockDim.x) {
@@ -416,7 +419,11 @@ __global__ void k_seg(const uint32_t *__restrict__ keys, const uint32_t *__restr
     for (int u = 1; u <= 8; ++u) {
       const int64_t i = i0 + u - 1;
       const uint32_t kk = k[u];
-      if (i >= n || (int64_t)kk >= npx) continue;
+      if (i >= n) continue;
+      if ((int64_t)kk >= npx) {
+        ddhf_check(false, flags);
+        continue;
+      }
       if (i == 0 || k[u - 1] != kk) seg_lo[kk] = (uint32_t)i;
       if (i == n - 1 || k[u + 1] != kk) seg_hi[kk] = (uint32_t)(i + 1);
     }
@@ -626,13 +633,13 @@ ddhf_status launch_scan_u64(Ctx *c, const uint64_t *in, uint64_t *out, int64_t n
 template <bool DROP, int BITS = 1>
 void launch_scatter(int bits, int64_t nch, cudaStream_t s, const uint32_t *kin,
                     const uint32_t *vin, int64_t n_in, const uint32_t *n_total, uint32_t *kout,
-                    uint32_t *vout, const uint32_t *hscan, int shift) {
+                    uint32_t *vout, const uint32_t *hscan, int shift, uint32_t *flags) {
   if constexpr (BITS <= kMaxDigitBits) {
     if (bits != BITS)
       return launch_scatter<DROP, BITS + 1>(bits, nch, s, kin, vin, n_in, n_total, kout, vout,
-                                            hscan, shift);
+                                            hscan, shift, flags);
     k_scatter<DROP, BITS><<<(unsigned)nch, kScatThreads, scatter_smem_bytes(1 << BITS), s>>>(
-        kin, vin, n_in, n_total, kout, vout, hscan, nch, shift);
+        kin, vin, n_in, n_total, kout, vout, hscan, nch, shift, flags);
   }
 }
 
@@ -694,9 +701,10 @@ ddhf_status bin_core(Ctx *c, Slot &sl, const RawIn &raw, int n_min, int heavy_mi
       DDHF_CUDA_TRY(c, scan_rec<uint32_t>(c->hist, c->hist, (int64_t)nb * nch, c->scan_part,
                                           pass == 0 ? ntot : nullptr, s));
       if (pass == 0)
-        launch_scatter<true>(bits, nch, s, in.pk, in.pv, n, ntot, ko, vo, c->hist, shift);
+        launch_scatter<true>(bits, nch, s, in.pk, in.pv, n, ntot, ko, vo, c->hist, shift,
+                             c->flags);
       else
-        launch_scatter<false>(bits, nch, s, ki, vi, n, ntot, ko, vo, c->hist, shift);
+        launch_scatter<false>(bits, nch, s, ki, vi, n, ntot, ko, vo, c->hist, shift, c->flags);
       DDHF_CUDA_TRY(c, cudaGetLastError());
       shift += bits;
     }
@@ -706,7 +714,7 @@ ddhf_status bin_core(Ctx *c, Slot &sl, const RawIn &raw, int n_min, int heavy_mi
   DDHF_CUDA_TRY(c, cudaMemsetAsync(c->seg_hi, 0, npx * sizeof(uint32_t), s));
   const int sm_blocks = c->num_sms * 8;
   if (nch > 0) {
-    k_seg<<<sm_blocks, 256, 0, s>>>(kfinal, ntot, c->seg_lo, c->seg_hi, npx);
+    k_seg<<<sm_blocks, 256, 0, s>>>(kfinal, ntot, c->seg_lo, c->seg_hi, npx, c->flags);
     DDHF_CUDA_TRY(c, cudaGetLastError());
   }
   unsigned pb = (unsigned)std::min<int64_t>(ceil_div(npx + 1, 256), sm_blocks);

@@ -121,11 +121,18 @@ __global__ void k_box_root_init(const int32_t *__restrict__ lab, int32_t *bx, in
 
 // Pixels of one component usually share a warp, so the bounds are first
 // reduced among the lanes with the same root and one lane updates the slot.
-__global__ void k_box_accum(const int32_t *__restrict__ lab, int32_t *bx, int W, int64_t npx) {
+// A label at or beyond npx (a caller's labels array) is skipped and raises
+// DDHF_FLAG_INPUT.
+__global__ void k_box_accum(const int32_t *__restrict__ lab, int32_t *bx, int W, int64_t npx,
+                            uint32_t *flags) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < npx; base += stride) {
     const int64_t i = base + threadIdx.x;
-    const int r = i < npx ? lab[i] : -1;
+    int r = i < npx ? lab[i] : -1;
+    if ((int64_t)r >= npx) {
+      atomicOr(flags, DDHF_FLAG_INPUT);
+      r = -1;
+    }
     const uint32_t peers = __match_any_sync(0xffffffffu, r);
     if (r < 0) continue;
     const int x = (int)(i % W), y = (int)(i / W);
@@ -436,7 +443,7 @@ ddhf_status launch_components(Ctx *c, const int32_t *labels, int32_t row0, ddhf_
   uint32_t *count = reinterpret_cast<uint32_t *>(n_out);
   DDHF_CUDA_TRY(c, cudaMemsetAsync(count, 0, sizeof(uint32_t), s));
   k_box_root_init<<<blocks, 256, 0, s>>>(labels, bx, c->W, npx);
-  k_box_accum<<<blocks, 256, 0, s>>>(labels, bx, c->W, npx);
+  k_box_accum<<<blocks, 256, 0, s>>>(labels, bx, c->W, npx, c->flags);
   k_comp_collect<<<blocks, 256, 0, s>>>(labels, bx, npx, c->W, row0, out, cap, count);
   DDHF_CUDA_TRY(c, cudaGetLastError());
   return DDHF_OK;
@@ -453,7 +460,7 @@ ddhf_status launch_boxes(Ctx *c, const int32_t *labels, ddhf_box *boxes, int32_t
   uint32_t *count = c->qctl + 9;
   DDHF_CUDA_TRY(c, cudaMemsetAsync(count, 0, sizeof(uint32_t), s));
   k_box_root_init<<<blocks, 256, 0, s>>>(labels, bx, c->W, npx);
-  k_box_accum<<<blocks, 256, 0, s>>>(labels, bx, c->W, npx);
+  k_box_accum<<<blocks, 256, 0, s>>>(labels, bx, c->W, npx, c->flags);
   k_box_collect<<<blocks, 256, 0, s>>>(labels, bx, npx, c->params.A_min, list, count);
   k_box_merge<<<1, kMergeThreads, 0, s>>>(list, list2, par, bx, count, c->params.alpha, boxes,
                                           cap, n_boxes, c->flags, c->loop_limit);

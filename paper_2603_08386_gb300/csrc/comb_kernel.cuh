@@ -42,6 +42,7 @@ __global__ void __launch_bounds__(128, NW == 2 ? 6 : (NW == 3 ? 8 : 1)) k_comb(c
     if (!CPLX && !spec_smem) {
       // a spectrum too large for shared memory is scored where it is
       CombOut o = comb_warp<NW>(row, cc, scratch);
+      if (!ddhf_check(o.w < 0 || (o.w >= cc.w_lo && o.w <= cc.w_hi), flags)) o.rotor = 0;
       if (lane == 0) {
         if (o.bad) atomicOr(flags, DDHF_FLAG_INTERNAL);
         if (log_sf) log_sf[a] = o.log_sf;
@@ -101,6 +102,7 @@ __global__ void __launch_bounds__(128, NW == 2 ? 6 : (NW == 3 ? 8 : 1)) k_comb(c
     }
     __syncwarp();
     CombOut o = comb_warp<NW>(Pw, cc, scratch);
+    if (!ddhf_check(o.w < 0 || (o.w >= cc.w_lo && o.w <= cc.w_hi), flags)) o.rotor = 0;
     if (lane == 0) {
       if (o.bad) atomicOr(flags, DDHF_FLAG_INTERNAL);
       if (log_sf) log_sf[a] = o.log_sf;

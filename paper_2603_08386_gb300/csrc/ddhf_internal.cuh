@@ -21,7 +21,22 @@ constexpr int kScatItems = 16;     // consecutive 32-event rows per scatter warp
 constexpr int kBinChunk = kScatThreads * kScatItems;  // 8192 events
 constexpr int kMaxBandWords = 8;   // comb rank band up to 256 positions
 constexpr uint32_t kSignBit = 0x80000000u;
+constexpr size_t kCanaryBytes = 256;        // guard region on each side of a buffer
+constexpr unsigned char kCanaryByte = 0xA5;
 constexpr uint32_t kDropKey = 0xffffffffu;  // pre-packed sort input: pair not kept
+
+// Invariant checks of the debug build (-DDDHF_BOUNDS_CHECK, made by
+// build(debug=True)): a failed check raises DDHF_FLAG_INTERNAL and the caller
+// skips the work item (never a trap or an assert). Release builds compile the
+// checks away.
+#ifdef DDHF_BOUNDS_CHECK
+__device__ __forceinline__ bool ddhf_check(bool ok, uint32_t *flags) {
+  if (!ok) atomicOr(flags, DDHF_FLAG_INTERNAL);
+  return ok;
+}
+#else
+__device__ __forceinline__ constexpr bool ddhf_check(bool, uint32_t *) { return true; }
+#endif
 
 // Per-window binning output and per-pixel results (one "slot" per window).
 struct Slot {
@@ -149,6 +164,13 @@ struct Ctx {
   int32_t *box_root = nullptr;   // [npx]
   int32_t *box_tmp = nullptr;    // [npx * 6]
   uint32_t *flags = nullptr;     // [1] DDHF_FLAG_* bits
+  // workspace buffers with guard bytes (kCanaryBytes of kCanaryByte before
+  // and after each), checked by ddhf_get_stats
+  struct Guarded {
+    void *user;        // the pointer the kernels use
+    size_t bytes;      // its size
+  };
+  std::vector<Guarded> guarded;
   float *soft_part = nullptr;    // [16 * npx + 16] soft-comb gradient partials
   float *pbuf = nullptr;         // [npx * pbuf_ld] spectra of one window (unfused detection)
   float *pbuf2 = nullptr;        // a second one for overlapped windows (tuning.overlap)

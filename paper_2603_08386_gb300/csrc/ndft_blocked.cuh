@@ -249,6 +249,7 @@ struct BlockedArgs {
   int warp_bytes;            // per-warp shared memory (bytes)
   int pw_offset;             // byte offset of the spectrum buffer inside a warp's area
   uint32_t *flags;
+  int64_t ev_cap;            // events each slot's event array holds (CSR bound)
 };
 
 // Bins [j_begin, j_end) of spectrum row `prow` from Pw (bin j_begin at Pw[0])
@@ -357,7 +358,8 @@ __device__ __forceinline__ void light_stream(const BlockedArgs &A, float4 *stage
       q_lo = v.offsets[key];
       q_hi = v.offsets[key + 1];
       const int cnt = (int)(q_hi - q_lo);
-      q_ok = cnt < A.heavy_min && !(A.skip_min > 0 && cnt >= A.skip_min);
+      q_ok = cnt < A.heavy_min && !(A.skip_min > 0 && cnt >= A.skip_min) &&
+             ddhf_check((int64_t)q_hi <= A.ev_cap, A.flags);
       if (q_ok && aq >= A.cap_px) {
         raise_flag(A.flags, DDHF_FLAG_CAPACITY);
         q_ok = false;
@@ -448,6 +450,7 @@ __global__ void __launch_bounds__(256, TB == 6 ? 2 : 1) k_blocked(BlockedArgs A)
     const uint32_t o0 = v.offsets[key];
     const int cnt = (int)(v.offsets[key + 1] - o0);
     if (A.skip_min > 0 && cnt >= A.skip_min) continue;
+    if (!ddhf_check((int64_t)o0 + cnt <= A.ev_cap, A.flags)) continue;
     const int rows_per_pass = 4 * TB;
     bool overflow = !FUSED && a >= A.cap_px;
     if (overflow) {
@@ -604,6 +607,7 @@ ddhf_status launch_blocked_t(Ctx *c, int n_slots, float *P, int64_t cap_px, cuda
   A.skip_min = skip_min;
   A.warp_bytes = blocked_warp_bytes<TB>(c, FUSED, NW, &A.pw_offset);
   A.flags = c->flags;
+  A.ev_cap = std::max<int64_t>(c->max_events, 1);
   const int wpb = c->tuning.warps_per_block;
   const size_t smem = (size_t)A.warp_bytes * wpb;
   auto kern = k_blocked<TB, NW, FUSED>;

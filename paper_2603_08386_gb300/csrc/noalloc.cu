@@ -151,7 +151,7 @@ ddhf_status scratch_for_current(NoAllocScratch **out) {
 
 template <int TB>
 ddhf_status launch_noalloc(NoAllocScratch *sp, const GridConst &g, float *P, int64_t cap_px,
-                           int64_t n_active, int num_sms, cudaStream_t s) {
+                           int64_t n_active, int64_t n_events, int num_sms, cudaStream_t s) {
   blocked::BlockedArgs A{};
   A.views = &sp->view;
   A.slot0 = 0;
@@ -174,6 +174,7 @@ ddhf_status launch_noalloc(NoAllocScratch *sp, const GridConst &g, float *P, int
   A.pw_offset = scratch;
   A.warp_bytes = scratch + 4 * TB * 32 * 4;
   A.flags = &sp->flags;
+  A.ev_cap = n_events;
   const size_t smem = (size_t)A.warp_bytes * kNoAllocWarps;
   auto kern = blocked::k_blocked<TB, 1, false>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
@@ -226,11 +227,11 @@ extern "C" ddhf_status ddhf_power_spectrum_noalloc(const ddhf_grid *grid, const 
   tb = tb <= 2 ? tb : tb <= 4 ? 4 : tb <= 6 ? 6 : 8;
   ddhf_status st;
   switch (tb) {
-    case 1: st = launch_noalloc<1>(sp, g, P, cap_px, n_active, num_sms, s); break;
-    case 2: st = launch_noalloc<2>(sp, g, P, cap_px, n_active, num_sms, s); break;
-    case 4: st = launch_noalloc<4>(sp, g, P, cap_px, n_active, num_sms, s); break;
-    case 6: st = launch_noalloc<6>(sp, g, P, cap_px, n_active, num_sms, s); break;
-    default: st = launch_noalloc<8>(sp, g, P, cap_px, n_active, num_sms, s); break;
+    case 1: st = launch_noalloc<1>(sp, g, P, cap_px, n_active, n_events, num_sms, s); break;
+    case 2: st = launch_noalloc<2>(sp, g, P, cap_px, n_active, n_events, num_sms, s); break;
+    case 4: st = launch_noalloc<4>(sp, g, P, cap_px, n_active, n_events, num_sms, s); break;
+    case 6: st = launch_noalloc<6>(sp, g, P, cap_px, n_active, n_events, num_sms, s); break;
+    default: st = launch_noalloc<8>(sp, g, P, cap_px, n_active, n_events, num_sms, s); break;
   }
   if (st != DDHF_OK) return st;
   if (flags_dev) {

@@ -51,6 +51,8 @@ struct SoftArgs {
   float *part;             // backward workspace [n_px][2 n_h]
   int backward;
   uint64_t barrett;        // floor((2^64-1) / 1e9)
+  int64_t npx;             // keys at or beyond it are skipped (DDHF_FLAG_INPUT)
+  uint32_t *flags;
 };
 
 template <bool BWD>
@@ -62,8 +64,11 @@ __global__ void __launch_bounds__(256) k_softcomb(SoftArgs A) {
   const int nq = 2 * A.Q + 1;
   for (int64_t a = wid; a < A.n_px; a += nwarps) {
     const uint32_t key = A.pixels[a];
-    const uint32_t o0 = A.offsets[key];
-    const int cnt = (int)(A.offsets[key + 1] - o0);
+    // a key off the sensor has no events: S = 0, zero gradients, flagged
+    const bool key_ok = (int64_t)key < A.npx;
+    if (!key_ok && lane == 0) atomicOr(A.flags, DDHF_FLAG_INPUT);
+    const uint32_t o0 = key_ok ? A.offsets[key] : 0u;
+    const int cnt = key_ok ? (int)(A.offsets[key + 1] - o0) : 0;
     // f0 in integer micro-Hz: every frequency h f0 + q delta is then an exact
     // integer number of micro-Hz, split into integer mHz (exact residue
     // a tau mod 1e9, as in the grid NDFT) plus a remainder below 1 mHz
@@ -340,6 +345,8 @@ extern "C" ddhf_status ddhf_softcomb(ddhf_ctx *h, int64_t n_px, const uint32_t *
   A.part = c->soft_part;  // [n_px][2 n_h] then the 2 n_h column sums
   A.backward = bwd;
   A.barrett = ~0ull / 1000000000ull;
+  A.npx = c->npx;
+  A.flags = c->flags;
   const int blocks = (int)std::min<int64_t>(ceil_div(n_px, 8), (int64_t)c->num_sms * 16);
   if (bwd) {
     k_softcomb<true><<<blocks, 256, 0, s>>>(A);

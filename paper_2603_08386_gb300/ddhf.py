@@ -15,7 +15,9 @@ import os
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libddhf.so")
+# DDHF_LIB names another build of the library (e.g. the debug build,
+# libddhf_debug.so); the default is the in-tree release build.
+LIB_PATH = os.environ.get("DDHF_LIB") or os.path.join(_HERE, "libddhf.so")
 
 DDHF_OK = 0
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "CAPACITY", 4: "TIMEOUT", 5: "UNSUPPORTED",
@@ -137,6 +139,7 @@ SIGNATURES = {
     "ddhf_export_labels": (_I32, [_VP, _I32, _VP, _VP]),
     "ddhf_box_frequencies": (_I32, [_VP, _I32, _VP, _VP, _I32, _VP, _VP, _VP]),
     "ddhf_debug_fail_alloc_after": (_I32, [_I32]),
+    "ddhf_debug_corrupt_guard": (_I32, [_VP, _I32]),
 }
 
 _lib = None
@@ -365,6 +368,11 @@ def ddhf_box_frequencies(ctx, slot, boxes, n_boxes, cap, f0_bin, snr=None, strea
     """Dominant bin (and SNR) of each detected box: its strongest rotor pixel."""
     _check(load().ddhf_box_frequencies(ctx, int(slot), _ptr(boxes), _ptr(n_boxes), int(cap),
                                        _ptr(f0_bin), _ptr(snr), _stream(stream)), ctx)
+
+
+def ddhf_debug_corrupt_guard(ctx, index):
+    """Test hook: overwrite one guard byte after workspace buffer `index`."""
+    _check(load().ddhf_debug_corrupt_guard(ctx, int(index)), ctx)
 
 
 def ddhf_enable_stage_timing(ctx, enable=True):

@@ -13,6 +13,7 @@ from paper_2603_08386_gb300 import ddhf, synth
 pytestmark = pytest.mark.gpu
 
 STATUS_TIMEOUT = 4
+STATUS_CUDA = 2
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -104,4 +105,53 @@ def test_injected_allocation_failure_releases_everything():
     c = ddhf.Context(s.W, s.H, s.grid, max_events=s.n)
     c.detect(x, y, t, p, s.t0, s.window_us)
     c.stats()
+    c.close()
+
+
+def test_guard_bytes_catch_a_write_outside_a_buffer():
+    # a full detection leaves every workspace guard intact; one guard byte
+    # overwritten from the host (inside the allocation: no stray device
+    # access) is reported by the next ddhf_get_stats as an internal error
+    s = synth.small_scene(31, W=64, H=48, n_noise=20_000, drone_px=120)
+    c = ddhf.Context(s.W, s.H, s.grid, max_events=s.n, max_windows=2)
+    x, y, t, p = ddhf.events_to_device(s)
+    c.detect(x, y, t, p, s.t0, s.window_us, cap=64)
+    st = c.stats()
+    assert st["device_flags"] == 0
+    for idx in (0, 7):
+        ddhf.ddhf_debug_corrupt_guard(c.h, idx)
+        st = c.stats(raise_on_flags=False)
+        assert st["device_flags"] & 4 and st["status"] == STATUS_CUDA
+    with pytest.raises(ddhf.DDHFError):
+        ddhf.ddhf_debug_corrupt_guard(c.h, 1 << 20)
+    c.close()
+
+
+def test_out_of_range_keys_and_labels_are_skipped_and_reported():
+    # caller-built device arrays with an index off the sensor: the kernels skip
+    # the entry (no access outside the arrays) and ddhf_get_stats reports
+    # DDHF_FLAG_INPUT as an invalid argument; the context stays usable
+    s = synth.small_scene(32, W=40, H=30, n_noise=6_000, drone_px=60)
+    c = ddhf.Context(s.W, s.H, s.grid, max_events=s.n)
+    x, y, t, p = ddhf.events_to_device(s)
+    c.bin_events(x, y, t, p, s.t0, s.window_us)
+    pix = c.csr()["active"][:8].clone()
+    pix[3] = s.W * s.H + 5
+    n = pix.numel()
+    ones = torch.ones(n, device="cuda")
+    S = torch.full((n,), float("nan"), device="cuda")
+    ddhf.ddhf_softcomb(c.h, pix, 150.0 * ones, 4, 2, 2.0, s.window_us / 2,
+                       torch.ones(4, device="cuda"), torch.full((4,), 2.0, device="cuda"), ones, S=S)
+    st = c.stats(raise_on_flags=False)
+    assert st["device_flags"] & 8 and st["status"] == 1  # DDHF_ERR_INVALID_ARG
+    assert float(S[3]) == 0.0 and torch.isfinite(S).all()
+    lab = torch.full((s.W * s.H,), -1, dtype=torch.int32, device="cuda")
+    lab[:4] = 0
+    lab[10] = s.W * s.H + 100
+    bx = torch.empty((16, 5), dtype=torch.int32, device="cuda")
+    nb = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ddhf.ddhf_boxes(c.h, lab, bx, 16, nb)
+    st = c.stats(raise_on_flags=False)
+    assert st["device_flags"] & 8 and st["status"] == 1
+    assert c.stats()["device_flags"] == 0  # reported once, then cleared
     c.close()
