@@ -395,6 +395,18 @@ def _oracle_chunk(args):
     return time.perf_counter() - t_0
 
 
+def _oracle_chunk_f32(args):
+    """One worker's share of the FP32 CPU baseline: the oracle's FP32 NDFT
+    (Eq. 6 in single precision) of each pixel of the subset."""
+    import oracle
+    npx, b, grid = args
+    t_0 = time.perf_counter()
+    offs = b["offsets"]
+    for k in range(npx):
+        oracle.ndft_f32(b["tau"][offs[k]:offs[k + 1]], b["pol"][offs[k]:offs[k + 1]], *grid)
+    return time.perf_counter() - t_0
+
+
 def _pixel_subset(b, pix):
     """The events of pixels `pix` of a binned window as a one-row sensor."""
     cnt = b["counts"][pix]
@@ -404,10 +416,12 @@ def _pixel_subset(b, pix):
     return dict(offsets=offs, tau=b["tau"][sel], pol=b["pol"][sel], counts=cnt)
 
 
-def oracle_all_cores(b, W, H, grid, n_pixels, seed=5, procs=None):
+def oracle_all_cores(b, W, H, grid, n_pixels, seed=5, procs=None, fp32_ndft=False):
     """The oracle on a seeded sample of active pixels split over every host
-    core (one spawned worker per core, each a single-threaded oracle call).
+    core (one spawned worker per core, each a single-threaded oracle call):
+    Eq. 6-11 in FP64, or (fp32_ndft) the FP32 NDFT alone.
     Returns (terms, wall seconds, pixels, workers)."""
+    work = _oracle_chunk_f32 if fp32_ndft else _oracle_chunk
     procs = procs or os.cpu_count() or 1
     act = np.flatnonzero(b["counts"] >= 6)
     rng = np.random.default_rng(seed)
@@ -416,9 +430,9 @@ def oracle_all_cores(b, W, H, grid, n_pixels, seed=5, procs=None):
     chunks = [c for c in np.array_split(pix, procs) if c.size]
     jobs = [(c.size, _pixel_subset(b, c), grid) for c in chunks]
     with mp.get_context("spawn").Pool(processes=len(chunks)) as pool:
-        pool.map(_oracle_chunk, [(1, _pixel_subset(b, chunks[0][:1]), grid)] * len(chunks))
+        pool.map(work, [(1, _pixel_subset(b, chunks[0][:1]), grid)] * len(chunks))
         t_0 = time.perf_counter()
-        pool.map(_oracle_chunk, jobs, chunksize=1)
+        pool.map(work, jobs, chunksize=1)
         wall = time.perf_counter() - t_0
     return terms, wall, int(pix.size), len(chunks)
 
@@ -833,6 +847,12 @@ def main():
                           f"core): FP64 NDFT + SF + comb (Eq. 6-11), {secs:.1f} s wall",
                    one_core=dict(value=tr1 / secs1, pixels=npix1, seconds=secs1),
                    host_cores=ncores)
+        tr2, secs2, npix2, nw2 = oracle_all_cores(b0, W, H, grid, 3000 * ncores, seed=7,
+                                                  fp32_ndft=True)
+        cpu["fp32_ndft"] = dict(value=tr2 / secs2, unit=UNIT, cores=nw2,
+                                sample=f"{npix2} seeded random active pixels of window 0, "
+                                       f"{nw2} spawned workers: the oracle's FP32 NDFT (Eq. 6 "
+                                       f"alone, single precision), {secs2:.1f} s wall")
     f_avg = statistics.mean(fused_ms)
     fused_mode = statistics.mean(spec_ms) == 0.0
     peak = peaks["ffma2_lane_per_s"] / 1e12

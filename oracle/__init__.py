@@ -11,6 +11,7 @@ the passage of arXiv 2603.08386 it restates:
 
   bin_events      Sec. 3.5 "Event processing" (sort by pixel, n_min)
   ndft            Sec. 3.3 Eq. 6 and P_k = |F_k|^2
+  ndft_f32        the same in FP32 (the benchmark's FP32 CPU baseline)
   ndft_at         Eq. 6 at arbitrary frequencies plus dF/df (soft comb)
   log_sf          Sec. 3.4 Eq. 7
   comb, comb_f32  Sec. 3.4 Eq. 8-11
@@ -72,6 +73,8 @@ def _load():
                                               ctypes.POINTER(c_i64)]
             lib.oracle_ndft.restype = None
             lib.oracle_ndft.argtypes = [c_i64, i64p, i8p, c_i64, c_i64, c_i64, c_i32, f64p, vp]
+            lib.oracle_ndft_f32.restype = None
+            lib.oracle_ndft_f32.argtypes = [c_i64, i64p, i8p, c_i64, c_i64, c_i64, c_i32, f32p]
             lib.oracle_ndft_at.restype = None
             lib.oracle_ndft_at.argtypes = [c_i64, i64p, i8p, c_f64, c_i32, f64p, f64p, vp]
             lib.oracle_log_sf.restype = c_f64
@@ -141,6 +144,16 @@ def ndft(tau, pol, a0, da, denom, n_bins, return_f=False):
                     P, _ptr(F))
     if return_f:
         return P, F[0::2] + 1j * F[1::2]
+    return P
+
+
+def ndft_f32(tau, pol, a0, da, denom, n_bins):
+    """The same power spectrum in single precision (the FP32 CPU baseline of
+    the benchmark; parity is always checked against the FP64 ndft)."""
+    lib = _load()
+    tau, pol = _c(tau, np.int64), _c(pol, np.int8)
+    P = np.zeros(int(n_bins), np.float32)
+    lib.oracle_ndft_f32(int(tau.shape[0]), tau, pol, int(a0), int(da), int(denom), int(n_bins), P)
     return P
 
 

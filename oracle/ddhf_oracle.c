@@ -115,6 +115,25 @@ void oracle_ndft(int64_t n, const int64_t *tau, const int8_t *pol, int64_t a0,
   }
 }
 
+/* The same sum in single precision, for the FP32 CPU baseline of the      */
+/* benchmark (not a reference: the parity tests use the FP64 version): the */
+/* exact integer residue, its phase rounded once to float, float sin/cos   */
+/* and float accumulation in event order.                                   */
+void oracle_ndft_f32(int64_t n, const int64_t *tau, const int8_t *pol, int64_t a0,
+                     int64_t da, int64_t denom, int32_t n_bins, float *P) {
+  for (int32_t j = 0; j < n_bins; ++j) {
+    int64_t a = a0 + (int64_t)j * da;
+    float re = 0.0f, im = 0.0f;
+    for (int64_t k = 0; k < n; ++k) {
+      int64_t r = phase_residue(a, tau[k], denom);
+      float theta = (float)(2.0 * M_PI * ((double)r / (double)denom));
+      re += (float)pol[k] * cosf(theta);
+      im -= (float)pol[k] * sinf(theta);
+    }
+    P[j] = re * re + im * im;
+  }
+}
+
 /* Same sum at arbitrary real frequencies f (Hz) with tau in microseconds,   */
 /* evaluated in FP64 with the frequency split as f = fi/1000 + fr where fi   */
 /* is an integer number of mHz (exact residue) and fr the remainder; used by */

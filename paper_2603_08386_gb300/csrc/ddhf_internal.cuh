@@ -84,7 +84,6 @@ struct GridConst {
   uint64_t barrett;   // floor((2^64 - 1) / denom)
   uint64_t a0_mod;    // a0 mod denom
   uint64_t da_mod;    // da mod denom
-  uint64_t da16_mod;  // 16 da mod denom
   uint64_t da32_mod;  // 32 da mod denom
   int32_t N;
   int32_t nbr;        // b-rows of the blocked form: ceil(N / 32)
@@ -112,7 +111,6 @@ inline GridConst make_grid_const(const ddhf_grid &g) {
   k.barrett = ~0ull / (uint64_t)g.denom;
   k.a0_mod = (uint64_t)g.a0 % (uint64_t)g.denom;
   k.da_mod = (uint64_t)g.da % (uint64_t)g.denom;
-  k.da16_mod = ((uint64_t)g.da * 16ull) % (uint64_t)g.denom;
   k.da32_mod = ((uint64_t)g.da * 32ull) % (uint64_t)g.denom;
   k.N = g.n_bins;
   k.nbr = (g.n_bins + 31) / 32;

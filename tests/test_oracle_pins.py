@@ -492,3 +492,16 @@ def test_box_frequencies_hand_case():
     fb, sb = oracle.box_frequencies(boxes, active, mask, snr, f0, W)
     np.testing.assert_array_equal(fb, [9, 7, 4, -1])
     np.testing.assert_array_equal(sb, np.float32([5.0, 3.0, 5.0, 0.0]))
+
+
+def test_ndft_f32_agrees_with_fp64():
+    # the FP32 CPU baseline computes Eq. 6 to FP32 accuracy: P(0) = (sum p)^2
+    # exactly for small n, and within 1e-5 of each row's peak of the FP64 sum
+    rng = np.random.default_rng(17)
+    for n in (1, 7, 40, 300):
+        tau = np.sort(rng.integers(0, 30_000, n)).astype(np.int64)
+        pol = rng.choice(np.array([-1, 1], np.int8), n)
+        P64 = oracle.ndft(tau, pol, 0, 2000, 1_000_000_000, 750)
+        P32 = oracle.ndft_f32(tau, pol, 0, 2000, 1_000_000_000, 750)
+        assert P32[0] == np.float32(float(pol.sum()) ** 2)
+        assert np.abs(P32 - P64).max() <= 1e-5 * P64.max()
