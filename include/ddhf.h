@@ -358,17 +358,22 @@ ddhf_status ddhf_export_scores(ddhf_ctx *ctx, int32_t slot, uint32_t *active, fl
                                ddhf_stream stream);
 
 /* Dominant frequency of each detection (Eq. 11 returns one per rotor pixel;
- * a box takes that of its strongest pixel): for box b < min(*n_boxes_dev, cap)
- * of slot w's last ddhf_detect / ddhf_detect_batch (boxes, n_boxes_dev: device
- * arrays as those calls wrote them), among the rotor pixels of slot w whose
- * (x, y) lies inside the box's inclusive bounds, the one with the largest SNR
- * (ties: the smallest pixel key); f0_bin[b] receives its dominant bin (Hz =
- * grid frequency of that bin) and snr[b] (nullable) its SNR, or -1 and 0 when
- * the box holds no rotor pixel. Device outputs of cap entries; entries from
- * min(*n_boxes_dev, cap) on are left unchanged. */
+ * a box summarises those of the rotor pixels inside it): for box b <
+ * min(*n_boxes_dev, cap) of slot w's last ddhf_detect / ddhf_detect_batch
+ * (boxes, n_boxes_dev: device arrays as those calls wrote them), over the
+ * rotor pixels of slot w whose (x, y) lies inside the box's inclusive bounds:
+ *   f0_bin[b]        the dominant bin of the one with the largest SNR (ties:
+ *                    the smallest pixel key), -1 when there is none;
+ *   snr[b]           its SNR, 0 when there is none (nullable);
+ *   f0_hz_median[b]  the lower median (rank floor((n-1)/2) of the n sorted
+ *                    values) of their dominant bins, as a frequency in Hz
+ *                    ((a0 + j da) 1e6 / denom), 0 when there is none
+ *                    (nullable).
+ * Device outputs of cap entries; entries from min(*n_boxes_dev, cap) on are
+ * left unchanged. */
 ddhf_status ddhf_box_frequencies(ddhf_ctx *ctx, int32_t slot, const ddhf_box *boxes,
                                  const int32_t *n_boxes_dev, int32_t cap, int32_t *f0_bin,
-                                 float *snr, ddhf_stream stream);
+                                 float *snr, float *f0_hz_median, ddhf_stream stream);
 
 /* The 8-connected labels (as ddhf_label writes them) of slot w's rotor mask
  * from the last ddhf_detect / ddhf_detect_batch (Sec. 3.5 "Segmentation mask

@@ -271,6 +271,23 @@ def softcomb(tau, pol, f0, w, sigma, delta, Q, B, tau_c=0.0):
                 dS_df=gf.reshape(nh, 2 * int(Q) + 1))
 
 
+def box_median_hz(boxes, active, mask, f0_bin, W, grid):
+    """Per box: the lower median (the element of rank floor((n-1)/2) of the n
+    sorted values) of the dominant bins of the rotor pixels inside it, as Hz
+    ((a0 + j da) 1e6 / denom for grid (a0, da, denom, n)); 0.0 without any."""
+    active = np.asarray(active, np.int64)
+    ys, xs = active // W, active % W
+    rot = np.asarray(mask, bool)[active]
+    a0, da, denom = (int(v) for v in grid[:3])
+    out = []
+    for b in np.asarray(boxes).reshape(-1, np.asarray(boxes).shape[-1]):
+        x0, y0, x1, y1 = (int(v) for v in b[:4])
+        sel = rot & (xs >= x0) & (xs <= x1) & (ys >= y0) & (ys <= y1)
+        v = np.sort(np.asarray(f0_bin)[sel])
+        out.append(0.0 if v.size == 0 else (a0 + int(v[(v.size - 1) // 2]) * da) * 1e6 / denom)
+    return np.array(out, np.float32)
+
+
 def box_frequencies(boxes, active, mask, snr, f0_bin, W):
     """Eq. 11 returns a dominant frequency per rotor pixel; a detection box
     takes that of its strongest rotor pixel: for each box (x0, y0, x1, y1,

@@ -960,7 +960,7 @@ ddhf_status ddhf_export_scores(ddhf_ctx *h, int32_t slot, uint32_t *active, floa
 
 ddhf_status ddhf_box_frequencies(ddhf_ctx *h, int32_t slot, const ddhf_box *boxes,
                                  const int32_t *n_boxes_dev, int32_t cap, int32_t *f0_bin,
-                                 float *snr, ddhf_stream stream) {
+                                 float *snr, float *f0_hz_median, ddhf_stream stream) {
   if (!h) return DDHF_ERR_INVALID_ARG;
   Ctx *c = &h->c;
   if (slot < 0 || slot >= c->max_windows) return fail(c, DDHF_ERR_INVALID_ARG, "slot out of range");
@@ -968,7 +968,7 @@ ddhf_status ddhf_box_frequencies(ddhf_ctx *h, int32_t slot, const ddhf_box *boxe
     return fail(c, DDHF_ERR_INVALID_ARG, "boxes, n_boxes_dev and f0_bin are required");
   cudaStream_t s = (cudaStream_t)stream;
   c->last_stream = s;
-  return launch_box_f0(c, slot, boxes, n_boxes_dev, cap, f0_bin, snr, s);
+  return launch_box_f0(c, slot, boxes, n_boxes_dev, cap, f0_bin, snr, f0_hz_median, s);
 }
 
 ddhf_status ddhf_export_labels(ddhf_ctx *h, int32_t slot, int32_t *labels, ddhf_stream stream) {

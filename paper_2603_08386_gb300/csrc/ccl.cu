@@ -365,10 +365,12 @@ ddhf_status launch_label(Ctx *c, const uint8_t *mask, int32_t *labels, uint64_t 
 
 // Dominant frequency of each box: block b scans the rows of box b; warp by
 // warp, a row's active pixels are the run of the (ascending) active list
-// between the keys y W + x0 and y W + x1, found by binary search, and each
-// rotor pixel offers (SNR bits, -active index) to a maximum; the winner's
-// dominant bin and SNR are written (-1 and 0 when the box holds no rotor
-// pixel).
+// between the keys y W + x0 and y W + x1, found by binary search. First pass:
+// each rotor pixel offers (SNR bits, -active index) to a maximum (the
+// strongest pixel) and is counted; then, when asked for, the lower median of
+// the rotor pixels' dominant bins by a two-digit radix selection (bins below
+// 2^14, 7 bits per pass, one more scan of the box per digit). A box without
+// rotor pixels gets bin -1, SNR 0 and median 0 Hz.
 __global__ void __launch_bounds__(256) k_box_f0(const uint32_t *__restrict__ active,
                                                 const uint64_t *__restrict__ counters,
                                                 const uint8_t *__restrict__ mask,
@@ -376,8 +378,13 @@ __global__ void __launch_bounds__(256) k_box_f0(const uint32_t *__restrict__ act
                                                 const int32_t *__restrict__ f0,
                                                 const ddhf_box *__restrict__ boxes,
                                                 const int32_t *__restrict__ n_boxes, int32_t cap,
-                                                int W, int H, int32_t *f0_out, float *snr_out) {
+                                                int W, int H, int32_t *f0_out, float *snr_out,
+                                                float *med_hz, int64_t g_a0, int64_t g_da,
+                                                int64_t g_denom, uint32_t *flags) {
   __shared__ unsigned long long red[8];
+  __shared__ uint32_t cnt[8];
+  __shared__ uint32_t hist[128];
+  __shared__ uint32_t sel[2];
   const int b = blockIdx.x;
   const int nb = min(*n_boxes, cap);
   if (b >= nb) return;
@@ -386,34 +393,48 @@ __global__ void __launch_bounds__(256) k_box_f0(const uint32_t *__restrict__ act
   const ddhf_box bx = boxes[b];
   const int x0 = max(bx.x0, 0), x1 = min(bx.x1, W - 1);
   const int y0 = max(bx.y0, 0), y1 = min(bx.y1, H - 1);
-  unsigned long long best = 0ull;
-  for (int y = y0 + warp; y <= y1 && x0 <= x1; y += 8) {
-    const uint32_t lo = (uint32_t)((int64_t)y * W + x0), hi = (uint32_t)((int64_t)y * W + x1);
-    // first index with active[i] >= lo
-    int64_t l = 0, r = n_act;
-    while (l < r) {
-      const int64_t m = (l + r) >> 1;
-      if (active[m] < lo) l = m + 1;
-      else r = m;
-    }
-    for (int64_t i = l + lane;; i += 32) {
-      const bool in = i < n_act && active[i] <= hi;
-      if (in && mask[active[i]]) {
-        const unsigned long long v =
-            ((unsigned long long)__float_as_uint(snr[i]) << 32) | (0xffffffffu - (uint32_t)i);
-        best = v > best ? v : best;
+  // fn(i) for every rotor pixel i (active index) inside the box
+  auto visit = [&](auto fn) {
+    for (int y = y0 + warp; y <= y1 && x0 <= x1; y += 8) {
+      const uint32_t lo = (uint32_t)((int64_t)y * W + x0), hi = (uint32_t)((int64_t)y * W + x1);
+      int64_t l = 0, r = n_act;  // first index with active[i] >= lo
+      while (l < r) {
+        const int64_t m = (l + r) >> 1;
+        if (active[m] < lo) l = m + 1;
+        else r = m;
       }
-      if (!__any_sync(0xffffffffu, in)) break;
+      for (int64_t i = l + lane;; i += 32) {
+        const bool in = i < n_act && active[i] <= hi;
+        if (in && mask[active[i]]) fn(i);
+        if (!__any_sync(0xffffffffu, in)) break;
+      }
     }
-  }
+  };
+  unsigned long long best = 0ull;
+  uint32_t n = 0;
+  visit([&](int64_t i) {
+    const unsigned long long v =
+        ((unsigned long long)__float_as_uint(snr[i]) << 32) | (0xffffffffu - (uint32_t)i);
+    best = v > best ? v : best;
+    ++n;
+  });
   for (int o = 16; o > 0; o >>= 1) {
     const unsigned long long u = __shfl_xor_sync(0xffffffffu, best, o);
     best = u > best ? u : best;
+    n += __shfl_xor_sync(0xffffffffu, n, o);
   }
-  if (lane == 0) red[warp] = best;
+  if (lane == 0) {
+    red[warp] = best;
+    cnt[warp] = n;
+  }
   __syncthreads();
+  best = red[0];
+  n = cnt[0];
+  for (int w = 1; w < 8; ++w) {
+    best = red[w] > best ? red[w] : best;
+    n += cnt[w];
+  }
   if (threadIdx.x == 0) {
-    for (int w = 1; w < 8; ++w) best = red[w] > best ? red[w] : best;
     if (best == 0ull) {
       f0_out[b] = -1;
       if (snr_out) snr_out[b] = 0.f;
@@ -423,14 +444,56 @@ __global__ void __launch_bounds__(256) k_box_f0(const uint32_t *__restrict__ act
       if (snr_out) snr_out[b] = snr[i];
     }
   }
+  if (!med_hz) return;
+  if (n == 0) {
+    if (threadIdx.x == 0) med_hz[b] = 0.f;
+    return;
+  }
+  // lower median: the element of rank (n - 1) / 2 of the dominant bins
+  uint32_t rank = (n - 1) / 2, prefix = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    const int shift = pass == 0 ? 7 : 0;
+    for (int k = threadIdx.x; k < 128; k += blockDim.x) hist[k] = 0;
+    __syncthreads();
+    visit([&](int64_t i) {
+      const uint32_t v = (uint32_t)f0[i];
+      if (!ddhf_check(v < (1u << 14), flags)) return;
+      if (pass == 1 && (v >> 7) != prefix) return;
+      atomicAdd(&hist[(v >> shift) & 127u], 1u);
+    });
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t run = 0;
+      int dsel = 127;
+      for (int k = 0; k < 128; ++k) {
+        if (rank < run + hist[k]) {
+          dsel = k;
+          break;
+        }
+        run += hist[k];
+      }
+      sel[0] = (uint32_t)dsel;
+      sel[1] = rank - run;
+    }
+    __syncthreads();
+    if (pass == 0) prefix = sel[0];
+    else prefix = (prefix << 7) | sel[0];
+    rank = sel[1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    med_hz[b] = (float)((double)(g_a0 + (int64_t)prefix * g_da) * 1e6 / (double)g_denom);
 }
 
 ddhf_status launch_box_f0(Ctx *c, int slot, const ddhf_box *boxes, const int32_t *n_boxes,
-                          int32_t cap, int32_t *f0_out, float *snr_out, cudaStream_t s) {
+                          int32_t cap, int32_t *f0_out, float *snr_out, float *med_hz,
+                          cudaStream_t s) {
   const Slot &sl = c->slots[slot];
+  // bin j at (a0 + j da) / denom cycles per microsecond
   if (cap > 0)
     k_box_f0<<<cap, 256, 0, s>>>(sl.active, sl.counters, sl.mask, sl.snr, sl.f0, boxes, n_boxes,
-                                 cap, c->W, c->H, f0_out, snr_out);
+                                 cap, c->W, c->H, f0_out, snr_out, med_hz, c->grid.a0, c->grid.da,
+                                 c->grid.denom, c->flags);
   DDHF_CUDA_TRY(c, cudaGetLastError());
   return DDHF_OK;
 }

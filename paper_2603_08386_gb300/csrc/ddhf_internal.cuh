@@ -334,7 +334,8 @@ void set_bin_attributes();
 ddhf_status launch_label(Ctx *c, const uint8_t *mask, int32_t *labels, uint64_t *n_fg,
                          cudaStream_t s);
 ddhf_status launch_box_f0(Ctx *c, int slot, const ddhf_box *boxes, const int32_t *n_boxes,
-                          int32_t cap, int32_t *f0_out, float *snr_out, cudaStream_t s);
+                          int32_t cap, int32_t *f0_out, float *snr_out, float *med_hz,
+                          cudaStream_t s);
 ddhf_status launch_components(Ctx *c, const int32_t *labels, int32_t row0, ddhf_component *out,
                               int32_t cap, int32_t *n_out, cudaStream_t s);
 ddhf_status launch_boxes(Ctx *c, const int32_t *labels, ddhf_box *boxes, int32_t cap,

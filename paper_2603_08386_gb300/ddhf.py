@@ -137,7 +137,7 @@ SIGNATURES = {
     "ddhf_slide_get_stats": (_I32, [_VP, ctypes.POINTER(ddhf_slide_stats)]),
     "ddhf_measure_pipes": (_I32, [ctypes.POINTER(ddhf_pipe_peaks), _I32, _VP]),
     "ddhf_export_labels": (_I32, [_VP, _I32, _VP, _VP]),
-    "ddhf_box_frequencies": (_I32, [_VP, _I32, _VP, _VP, _I32, _VP, _VP, _VP]),
+    "ddhf_box_frequencies": (_I32, [_VP, _I32, _VP, _VP, _I32, _VP, _VP, _VP, _VP]),
     "ddhf_debug_fail_alloc_after": (_I32, [_I32]),
     "ddhf_debug_corrupt_guard": (_I32, [_VP, _I32]),
 }
@@ -364,10 +364,13 @@ def ddhf_export_labels(ctx, slot, labels, stream=None):
     _check(load().ddhf_export_labels(ctx, int(slot), _ptr(labels), _stream(stream)), ctx)
 
 
-def ddhf_box_frequencies(ctx, slot, boxes, n_boxes, cap, f0_bin, snr=None, stream=None):
-    """Dominant bin (and SNR) of each detected box: its strongest rotor pixel."""
+def ddhf_box_frequencies(ctx, slot, boxes, n_boxes, cap, f0_bin, snr=None, f0_hz_median=None,
+                         stream=None):
+    """Per detected box: the dominant bin and SNR of its strongest rotor pixel
+    and the lower median (Hz) of its rotor pixels' dominant frequencies."""
     _check(load().ddhf_box_frequencies(ctx, int(slot), _ptr(boxes), _ptr(n_boxes), int(cap),
-                                       _ptr(f0_bin), _ptr(snr), _stream(stream)), ctx)
+                                       _ptr(f0_bin), _ptr(snr), _ptr(f0_hz_median),
+                                       _stream(stream)), ctx)
 
 
 def ddhf_debug_corrupt_guard(ctx, index):

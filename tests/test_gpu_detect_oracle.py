@@ -57,7 +57,8 @@ def test_labelled_detection_matches_oracle(seed, prm):
     sc = c.scores()
     f0b = torch.full((256,), -7, dtype=torch.int32, device="cuda")
     snrb = torch.zeros(256, device="cuda")
-    ddhf.ddhf_box_frequencies(c.h, 0, bx, nb, 256, f0b, snrb)
+    medb = torch.full((256,), -3.0, device="cuda")
+    ddhf.ddhf_box_frequencies(c.h, 0, bx, nb, 256, f0b, snrb, medb)
     P32 = c.power_spectrum("hybrid").cpu().numpy()  # the spectra the detection scored
     st = c.stats()
     c.close()
@@ -76,6 +77,9 @@ def test_labelled_detection_matches_oracle(seed, prm):
     np.testing.assert_array_equal(f0b[:n].cpu().numpy(), rf)
     np.testing.assert_array_equal(snrb[:n].cpu().numpy().view(np.int32), rs.view(np.int32))
     assert (rf >= 0).all() and (f0b[n:].cpu().numpy() == -7).all()
+    rm = oracle.box_median_hz(bx[:n].cpu().numpy(), act, gmask, sc["f0_bin"].cpu().numpy(), s.W,
+                              s.grid)
+    np.testing.assert_array_equal(medb[:n].cpu().numpy(), rm)
     # rotor bits against the FP64 oracle outside the margins
     b = oracle.bin_events(s.W, s.H, s.x, s.y, s.t, s.p, s.t0, s.window_us)
     np.testing.assert_array_equal(np.flatnonzero(b["counts"] >= prm["n_min"]), act)

@@ -492,6 +492,13 @@ def test_box_frequencies_hand_case():
     fb, sb = oracle.box_frequencies(boxes, active, mask, snr, f0, W)
     np.testing.assert_array_equal(fb, [9, 7, 4, -1])
     np.testing.assert_array_equal(sb, np.float32([5.0, 3.0, 5.0, 0.0]))
+    # lower medians of the rotor bins (7, 9, 4 -> sorted 4, 7, 9 -> 7; 7; 4; none)
+    # on a 2 Hz grid from 0 (bin j = 2 j Hz)
+    med = oracle.box_median_hz(boxes, active, mask, f0, W, (0, 2000, 1_000_000_000, 750))
+    np.testing.assert_array_equal(med, np.float32([14.0, 14.0, 8.0, 0.0]))
+    two = oracle.box_median_hz(np.array([[1, 1, 3, 1, 0]]), active, mask, f0, W,
+                               (0, 2000, 1_000_000_000, 750))
+    np.testing.assert_array_equal(two, np.float32([14.0]))  # bins 7, 9: lower median 7
 
 
 def test_ndft_f32_agrees_with_fp64():

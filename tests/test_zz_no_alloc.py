@@ -74,6 +74,28 @@ def test_noalloc_equals_context_spectra_twice_without_allocating():
             assert torch.equal(P, ref)
 
 
+def test_noalloc_lists_out_of_order_give_the_same_rows():
+    # a caller's active list need not follow the event array's order: shuffled,
+    # with one pixel listed twice, the spectrum kernel streams such runs one
+    # pixel at a time, and each row must be its pixel's row bit for bit
+    s = _scene(6, 750, 2)
+    csr, ref = _reference(s)
+    act = csr["active"].long()
+    na = act.numel()
+    rng = np.random.default_rng(9)
+    perm = torch.from_numpy(rng.permutation(na)).cuda()
+    perm = torch.cat([perm, perm[:1]])  # a duplicate entry: overlapping ranges
+    act2 = act[perm].to(torch.int32).contiguous()
+    P = torch.full((perm.numel(), ref.shape[1]), -1.0, dtype=torch.float32, device="cuda")
+    flags = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    ddhf.ddhf_power_spectrum_noalloc(ddhf.make_grid(*s.grid), csr["offsets"], csr["ev"],
+                                     csr["n_valid"], act2, perm.numel(), P, perm.numel(),
+                                     flags=flags)
+    torch.cuda.synchronize()
+    assert int(flags.item()) == 0
+    assert torch.equal(P, ref[perm])
+
+
 def test_noalloc_rejects_sizes_beyond_its_limit():
     build.build()
     g = ddhf.make_grid(0, 2000, synth.HZ_DENOM, 750)
