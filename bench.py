@@ -643,8 +643,23 @@ def main():
         e1.record()
         torch.cuda.synchronize()
         e2e_ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
+        # the host-to-device copies alone (same pinned buffers, one stream):
+        # the bandwidth that bounds the end-to-end rate when it is below the
+        # step's own rate
+        dst = [tuple(torch.empty_like(a, device="cuda") for a in hw) for hw in host]
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record()
+        for hw, dw in zip(host, dst):
+            for a, b_ in zip(hw, dw):
+                b_.copy_(a, non_blocking=True)
+        c1.record()
+        torch.cuda.synchronize()
+        h2d_ms = c0.elapsed_time(c1)
+        del dst
         e2e = dict(value=job_throughput(terms_step, world, e2e_steps, e2e_ms), unit=UNIT,
                    h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h, steps=e2e_steps,
+                   ms_per_step=e2e_ms / e2e_steps, h2d_alone_ms_per_step=h2d_ms,
+                   h2d_alone_gbs=h2d / (h2d_ms * 1e-3) / 1e9,
                    call="ddhf_detect_batch_host (pinned host events in, host boxes out)")
     # ------------------------------------------------------------ one-window latency
     # a single 1280x720 window (stream 0, window 0) through the graph-replayed

@@ -396,17 +396,18 @@ ddhf_status ddhf_stage_times(ddhf_ctx *ctx, float *out_ms);
 
 /* ddhf_detect over n_windows windows whose event arrays are in HOST memory
  * (windows[w].x/y/t_us/p host pointers; page-locked memory lets the copies
- * overlap the kernels): window w + 1's events are copied into one of two
- * context-owned device staging buffers on an internal copy stream while
- * window w is processed on `stream` (the same kernels as ddhf_detect, one
- * window at a time in the context's first slot). Results go to host memory:
- * boxes_host[n_windows * cap] (window w at boxes_host + w * cap),
- * n_boxes_host[n_windows], masks_host[n_windows * W * H] (nullable). The call
- * returns once the work is enqueued; host inputs must stay valid and outputs
- * are complete when `stream` has finished. The copies are ordered after the
- * work already queued on `stream`. Any n_windows >= 1 (max_windows does not
- * apply); the first call allocates the staging buffers (2 x max_events
- * events). */
+ * overlap the kernels). The windows go through in groups of G = min(8,
+ * max_windows, n_windows): group k + 1's events are copied into one of two
+ * context-owned device staging sets on an internal copy stream while group k
+ * is processed on `stream` by the batched detection (the kernels and tuning
+ * of ddhf_detect_batch, one slot per window of the group, launched without a
+ * graph). Results go to host memory: boxes_host[n_windows * cap] (window w
+ * at boxes_host + w * cap), n_boxes_host[n_windows], masks_host[n_windows *
+ * W * H] (nullable). The call returns once the work is enqueued; host inputs
+ * must stay valid and outputs are complete when `stream` has finished. The
+ * copies are ordered after the work already queued on `stream`. Any
+ * n_windows >= 1; the first call allocates the staging sets (2 x G x
+ * max_events events) and the device box buffers. */
 ddhf_status ddhf_detect_batch_host(ddhf_ctx *ctx, const ddhf_window *windows, int32_t n_windows,
                                    ddhf_box *boxes_host, int32_t cap, int32_t *n_boxes_host,
                                    uint8_t *masks_host, ddhf_stream stream);

@@ -846,6 +846,9 @@ ddhf_status ddhf_detect_batch(ddhf_ctx *h, const ddhf_window *wins, int32_t n_wi
   return DDHF_OK;
 }
 
+// Windows per group of ddhf_detect_batch_host.
+constexpr int kHostGroup = 8;
+
 // Stage sizes of one window's raw events: x, y int16, t int64, p int8.
 static int64_t host_stage_bytes(int64_t n) {
   const int64_t a = (2 * n + 255) & ~(int64_t)255;
@@ -863,22 +866,33 @@ ddhf_status ddhf_detect_batch_host(ddhf_ctx *h, const ddhf_window *wins, int32_t
   for (int w = 0; w < n_windows; ++w)
     DDHF_TRY(check_window(c, wins[w].x, wins[w].y, wins[w].t_us, wins[w].p, wins[w].n,
                           wins[w].window_us));
-  // workspace: staging for max_events, a box buffer for cap (grown on demand)
-  if (c->hstage_cap < c->max_events) {
+  // windows go through in groups of G (up to kHostGroup, at most max_windows)
+  // by the batched detection; the next group's events are copied meanwhile
+  const int G = std::min<int>(std::min(n_windows, kHostGroup), c->max_windows);
+  const int64_t per_win = host_stage_bytes(std::max<int64_t>(c->max_events, 1));
+  // workspace: two staging sets of G windows, box buffers for G x cap (grown on demand)
+  if (c->hstage_cap < c->max_events || c->hstage_windows < G) {
     for (auto &p : c->hstage) {
       if (p) cudaFree(p);
       p = nullptr;
-      DDHF_CUDA_TRY(c, cudaMalloc(&p, host_stage_bytes(std::max<int64_t>(c->max_events, 1))));
+      DDHF_CUDA_TRY(c, cudaMalloc(&p, (size_t)per_win * G));
     }
     c->hstage_cap = c->max_events;
+    c->hstage_windows = G;
   }
-  if (c->hbox_cap < std::max(cap, 1)) {
+  const int64_t box_need = (int64_t)std::max(cap, 1) * G;
+  if (c->hbox_cap < box_need) {
     if (c->hbox) cudaFree(c->hbox);
     c->hbox = nullptr;
-    DDHF_CUDA_TRY(c, cudaMalloc(&c->hbox, sizeof(ddhf_box) * std::max(cap, 1)));
-    c->hbox_cap = std::max(cap, 1);
+    DDHF_CUDA_TRY(c, cudaMalloc(&c->hbox, sizeof(ddhf_box) * box_need));
+    c->hbox_cap = box_need;
   }
-  if (!c->hnbox) DDHF_CUDA_TRY(c, cudaMalloc(&c->hnbox, sizeof(int32_t)));
+  if (c->hnbox_cap < G) {
+    if (c->hnbox) cudaFree(c->hnbox);
+    c->hnbox = nullptr;
+    DDHF_CUDA_TRY(c, cudaMalloc(&c->hnbox, sizeof(int32_t) * G));
+    c->hnbox_cap = G;
+  }
   if (!c->copy_stream)
     DDHF_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
   for (cudaEvent_t *e : {&c->h_ready[0], &c->h_ready[1], &c->h_free[0], &c->h_free[1],
@@ -890,42 +904,47 @@ ddhf_status ddhf_detect_batch_host(ddhf_ctx *h, const ddhf_window *wins, int32_t
   // the copies are ordered after the caller's earlier work on `stream`
   DDHF_CUDA_TRY(c, cudaEventRecord(c->h_start, s));
   DDHF_CUDA_TRY(c, cudaStreamWaitEvent(cs, c->h_start, 0));
-  for (int w = 0; w < n_windows; ++w) {
-    const int b = w & 1;
-    const ddhf_window &W = wins[w];
-    const int64_t n = W.n;
-    const int64_t ab2 = (2 * c->hstage_cap + 255) & ~(int64_t)255;
-    const int64_t ab8 = (8 * c->hstage_cap + 255) & ~(int64_t)255;
-    char *base = static_cast<char *>(c->hstage[b]);
-    int16_t *dx = reinterpret_cast<int16_t *>(base);
-    int16_t *dy = reinterpret_cast<int16_t *>(base + ab2);
-    int64_t *dt = reinterpret_cast<int64_t *>(base + 2 * ab2);
-    int8_t *dp = reinterpret_cast<int8_t *>(base + 2 * ab2 + ab8);
-    // window w's events into staging set b once window w - 2 has finished with it
-    if (w >= 2) DDHF_CUDA_TRY(c, cudaStreamWaitEvent(cs, c->h_free[b], 0));
-    if (n > 0) {
-      DDHF_CUDA_TRY(c, cudaMemcpyAsync(dx, W.x, 2 * n, cudaMemcpyHostToDevice, cs));
-      DDHF_CUDA_TRY(c, cudaMemcpyAsync(dy, W.y, 2 * n, cudaMemcpyHostToDevice, cs));
-      DDHF_CUDA_TRY(c, cudaMemcpyAsync(dt, W.t_us, 8 * n, cudaMemcpyHostToDevice, cs));
-      DDHF_CUDA_TRY(c, cudaMemcpyAsync(dp, W.p, n, cudaMemcpyHostToDevice, cs));
+  const int64_t ab2 = (2 * c->hstage_cap + 255) & ~(int64_t)255;
+  const int64_t ab8 = (8 * c->hstage_cap + 255) & ~(int64_t)255;
+  ddhf_window dw[kHostGroup];
+  for (int g0 = 0, k = 0; g0 < n_windows; g0 += G, ++k) {
+    const int b = k & 1;
+    const int ng = std::min(G, n_windows - g0);
+    // group k's events into staging set b once group k - 2 has finished with it
+    if (k >= 2) DDHF_CUDA_TRY(c, cudaStreamWaitEvent(cs, c->h_free[b], 0));
+    for (int i = 0; i < ng; ++i) {
+      const ddhf_window &W = wins[g0 + i];
+      const int64_t n = W.n;
+      char *base = static_cast<char *>(c->hstage[b]) + (int64_t)i * per_win;
+      int16_t *dx = reinterpret_cast<int16_t *>(base);
+      int16_t *dy = reinterpret_cast<int16_t *>(base + ab2);
+      int64_t *dt = reinterpret_cast<int64_t *>(base + 2 * ab2);
+      int8_t *dp = reinterpret_cast<int8_t *>(base + 2 * ab2 + ab8);
+      if (n > 0) {
+        DDHF_CUDA_TRY(c, cudaMemcpyAsync(dx, W.x, 2 * n, cudaMemcpyHostToDevice, cs));
+        DDHF_CUDA_TRY(c, cudaMemcpyAsync(dy, W.y, 2 * n, cudaMemcpyHostToDevice, cs));
+        DDHF_CUDA_TRY(c, cudaMemcpyAsync(dt, W.t_us, 8 * n, cudaMemcpyHostToDevice, cs));
+        DDHF_CUDA_TRY(c, cudaMemcpyAsync(dp, W.p, n, cudaMemcpyHostToDevice, cs));
+      }
+      dw[i] = W;
+      dw[i].x = dx;
+      dw[i].y = dy;
+      dw[i].t_us = dt;
+      dw[i].p = dp;
     }
     DDHF_CUDA_TRY(c, cudaEventRecord(c->h_ready[b], cs));
     DDHF_CUDA_TRY(c, cudaStreamWaitEvent(s, c->h_ready[b], 0));
-    ddhf_window dw = W;
-    dw.x = dx;
-    dw.y = dy;
-    dw.t_us = dt;
-    dw.p = dp;
-    DDHF_TRY(run_detect(c, &dw, 1, c->hbox, cap, c->hnbox, nullptr, s));
+    DDHF_TRY(run_detect(c, dw, ng, c->hbox, cap, c->hnbox, nullptr, s));
     DDHF_CUDA_TRY(c, cudaEventRecord(c->h_free[b], s));
     if (cap > 0)
-      DDHF_CUDA_TRY(c, cudaMemcpyAsync(boxes_host + (int64_t)w * cap, c->hbox,
-                                       sizeof(ddhf_box) * cap, cudaMemcpyDeviceToHost, s));
-    DDHF_CUDA_TRY(c, cudaMemcpyAsync(n_boxes_host + w, c->hnbox, sizeof(int32_t),
+      DDHF_CUDA_TRY(c, cudaMemcpyAsync(boxes_host + (int64_t)g0 * cap, c->hbox,
+                                       sizeof(ddhf_box) * cap * ng, cudaMemcpyDeviceToHost, s));
+    DDHF_CUDA_TRY(c, cudaMemcpyAsync(n_boxes_host + g0, c->hnbox, sizeof(int32_t) * ng,
                                      cudaMemcpyDeviceToHost, s));
     if (masks_host)
-      DDHF_CUDA_TRY(c, cudaMemcpyAsync(masks_host + (int64_t)w * c->npx, c->slots[0].mask,
-                                       c->npx, cudaMemcpyDeviceToHost, s));
+      for (int i = 0; i < ng; ++i)
+        DDHF_CUDA_TRY(c, cudaMemcpyAsync(masks_host + (int64_t)(g0 + i) * c->npx,
+                                         c->slots[i].mask, c->npx, cudaMemcpyDeviceToHost, s));
   }
   c->binned = true;
   return DDHF_OK;

@@ -190,12 +190,14 @@ struct Ctx {
   // for one window's raw events, a copy stream and its events, and the
   // device box buffer of one window
   void *hstage[2] = {nullptr, nullptr};  // x int16, y int16, t int64, p int8 each
-  int64_t hstage_cap = 0;                // events per staging set
+  int64_t hstage_cap = 0;                // events per window of a staging set
+  int hstage_windows = 0;                // windows per staging set
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t h_ready[2] = {nullptr, nullptr}, h_free[2] = {nullptr, nullptr}, h_start = nullptr;
   ddhf_box *hbox = nullptr;
   int32_t *hnbox = nullptr;
-  int32_t hbox_cap = 0;
+  int64_t hbox_cap = 0;                  // boxes the device box buffer holds
+  int32_t hnbox_cap = 0;
   cudaEvent_t stage_ev[4] = {nullptr, nullptr, nullptr, nullptr};
   std::vector<cudaEvent_t> win_ev;  // 5 per window (unfused path)
   // graph cache of ddhf_detect_batch

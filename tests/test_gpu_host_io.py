@@ -1,7 +1,8 @@
 """Host-input batch detection: events in page-locked host memory, copies of
-the next window overlapped with the current one; boxes, counts and masks must
-equal the device-input path exactly, for more windows than the context's
-window slots and with both detection tunings."""
+the next group of windows overlapped with the current one; boxes, counts and
+masks must equal the device-input path exactly, for more windows than the
+context's window slots, with one and with three slots (groups of 3 and 2) and
+with the fused, unfused and overlapped tunings."""
 import numpy as np
 import pytest
 import torch
@@ -11,14 +12,16 @@ from paper_2603_08386_gb300 import ddhf, synth
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("fuse", [0, 1])
-def test_host_batch_equals_device_path(fuse):
+@pytest.mark.parametrize("fuse,max_windows,overlap", [(0, 1, 0), (1, 1, 0), (0, 3, 1), (1, 3, 0)])
+def test_host_batch_equals_device_path(fuse, max_windows, overlap):
+    # with 3 window slots the 5 windows go through as groups of 3 and 2 by the
+    # batched detection (the overlapped form with overlap 1)
     scenes = [synth.small_scene(80 + i, W=48, H=40, n_noise=15_000 + 4000 * i, drone_px=120,
                                 grid=synth.hz_grid(0, 2, 750)) for i in range(5)]
     W, H, cap = 48, 40, 64
     maxev = max(sc.n for sc in scenes)
-    c = ddhf.Context(W, H, scenes[0].grid, max_events=maxev, max_windows=1)
-    c.set_tuning(fuse=fuse)
+    c = ddhf.Context(W, H, scenes[0].grid, max_events=maxev, max_windows=max_windows)
+    c.set_tuning(fuse=fuse, overlap=overlap)
     want = []
     bx = torch.empty((cap, 5), dtype=torch.int32, device="cuda")
     nb = torch.zeros(1, dtype=torch.int32, device="cuda")
