@@ -712,11 +712,11 @@ def main():
         forms = dict(window="stream 0, window 0", active_pixels=na0,
                      terms=terms_of(w0, W, H, nb))
         # the blocked kernel alone takes every pixel, so its own heavy threshold
-        # (block-per-pixel from heavy_min events) is chosen here among three
+        # (block-per-pixel from heavy_min events) is chosen here among a few
         # values; the step's tuning picks heavy_min for the pixels that the
         # hybrid route leaves to it
         runs = [("blocked", ddhf.FORM["blocked"], dict(base, hybrid_min=0, heavy_min=h))
-                for h in sorted({256, 1024, int(base.get("heavy_min", 1024))})]
+                for h in sorted({128, 256, 512, 1024, int(base.get("heavy_min", 1024))})]
         runs.append(("hybrid", ddhf.FORM["hybrid"], dict(base, hybrid_min=hm)))
         for name, form, tun in runs:
             fc.set_tuning(**tun)
