@@ -396,12 +396,12 @@ ddhf_status ddhf_stage_times(ddhf_ctx *ctx, float *out_ms);
 
 /* ddhf_detect over n_windows windows whose event arrays are in HOST memory
  * (windows[w].x/y/t_us/p host pointers; page-locked memory lets the copies
- * overlap the kernels). The windows go through in groups of G = min(8,
+ * overlap the kernels). The windows go through in groups of G = min(16,
  * max_windows, n_windows): group k + 1's events are copied into one of two
  * context-owned device staging sets on an internal copy stream while group k
  * is processed on `stream` by the batched detection (the kernels and tuning
  * of ddhf_detect_batch, one slot per window of the group, launched without a
- * graph). Results go to host memory: boxes_host[n_windows * cap] (window w
+ * graph); each window's binning waits only for that window's copy. Results go to host memory: boxes_host[n_windows * cap] (window w
  * at boxes_host + w * cap), n_boxes_host[n_windows], masks_host[n_windows *
  * W * H] (nullable). The call returns once the work is enqueued; host inputs
  * must stay valid and outputs are complete when `stream` has finished. The

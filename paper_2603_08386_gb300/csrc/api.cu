@@ -168,6 +168,11 @@ void free_all(Ctx *c) {
       cudaEventDestroy(*e);
       *e = nullptr;
     }
+  for (cudaEvent_t &e : c->h_win)
+    if (e) {
+      cudaEventDestroy(e);
+      e = nullptr;
+    }
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   c->graph_exec = nullptr;
   for (auto &e : c->stage_ev)
@@ -272,8 +277,11 @@ cudaError_t record_event(cudaEvent_t ev, cudaStream_t s) {
 
 cudaError_t record_stage(Ctx *c, int i, cudaStream_t s) { return record_event(c->stage_ev[i], s); }
 
+// ready (nullable): per window, an event that `s` waits for before binning it
+// (the host-buffer path: that window's copy).
 ddhf_status run_detect(Ctx *c, const ddhf_window *wins, int nw, ddhf_box *boxes, int32_t cap,
-                       int32_t *n_boxes_dev, uint8_t *masks_out, cudaStream_t s) {
+                       int32_t *n_boxes_dev, uint8_t *masks_out, cudaStream_t s,
+                       const cudaEvent_t *ready = nullptr) {
   if (c->timing) DDHF_CUDA_TRY(c, record_stage(c, 0, s));
   const bool fused = c->tuning.fuse != 0 || !c->pbuf;
   if (fused) {
@@ -282,6 +290,7 @@ ddhf_status run_detect(Ctx *c, const ddhf_window *wins, int nw, ddhf_box *boxes,
       const ddhf_window &W = wins[w];
       NvtxRange r("ddhf binning");
       DDHF_CUDA_TRY(c, cudaMemsetAsync(c->slots[w].mask, 0, c->npx, s));
+      if (ready) DDHF_CUDA_TRY(c, cudaStreamWaitEvent(s, ready[w], 0));
       DDHF_TRY(bin_into(c, w, W.x, W.y, W.t_us, W.p, W.n, W.t0_us, W.window_us, s));
     }
     if (c->timing) DDHF_CUDA_TRY(c, record_stage(c, 1, s));
@@ -305,7 +314,8 @@ ddhf_status run_detect(Ctx *c, const ddhf_window *wins, int nw, ddhf_box *boxes,
       {
         NvtxRange r("ddhf binning");
         DDHF_CUDA_TRY(c, cudaMemsetAsync(c->qctl, 0, sizeof(uint32_t), s));
-        DDHF_TRY(bin_into(c, w, W.x, W.y, W.t_us, W.p, W.n, W.t0_us, W.window_us, s));
+        if (ready) DDHF_CUDA_TRY(c, cudaStreamWaitEvent(s, ready[w], 0));
+      DDHF_TRY(bin_into(c, w, W.x, W.y, W.t_us, W.p, W.n, W.t0_us, W.window_us, s));
       }
       if (we) DDHF_CUDA_TRY(c, record_event(we[1], s));
       if (w >= 2) DDHF_CUDA_TRY(c, cudaStreamWaitEvent(s, c->ov_comb[w & 1], 0));
@@ -337,7 +347,8 @@ ddhf_status run_detect(Ctx *c, const ddhf_window *wins, int nw, ddhf_box *boxes,
       {
         NvtxRange r("ddhf binning");
         DDHF_CUDA_TRY(c, cudaMemsetAsync(c->qctl, 0, sizeof(uint32_t), s));
-        DDHF_TRY(bin_into(c, w, W.x, W.y, W.t_us, W.p, W.n, W.t0_us, W.window_us, s));
+        if (ready) DDHF_CUDA_TRY(c, cudaStreamWaitEvent(s, ready[w], 0));
+      DDHF_TRY(bin_into(c, w, W.x, W.y, W.t_us, W.p, W.n, W.t0_us, W.window_us, s));
       }
       if (we) DDHF_CUDA_TRY(c, record_event(we[1], s));
       Slot &sl = c->slots[w];
@@ -847,7 +858,9 @@ ddhf_status ddhf_detect_batch(ddhf_ctx *h, const ddhf_window *wins, int32_t n_wi
 }
 
 // Windows per group of ddhf_detect_batch_host.
-constexpr int kHostGroup = 8;
+constexpr int kHostGroup = 16;
+static_assert(2 * kHostGroup <= (int)(sizeof(Ctx::h_win) / sizeof(cudaEvent_t)),
+              "one copy event per staged window");
 
 // Stage sizes of one window's raw events: x, y int16, t int64, p int8.
 static int64_t host_stage_bytes(int64_t n) {
@@ -898,6 +911,8 @@ ddhf_status ddhf_detect_batch_host(ddhf_ctx *h, const ddhf_window *wins, int32_t
   for (cudaEvent_t *e : {&c->h_ready[0], &c->h_ready[1], &c->h_free[0], &c->h_free[1],
                          &c->h_start})
     if (!*e) DDHF_CUDA_TRY(c, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  for (cudaEvent_t &e : c->h_win)
+    if (!e) DDHF_CUDA_TRY(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   cudaStream_t s = (cudaStream_t)stream;
   cudaStream_t cs = c->copy_stream;
   c->last_stream = s;
@@ -907,6 +922,8 @@ ddhf_status ddhf_detect_batch_host(ddhf_ctx *h, const ddhf_window *wins, int32_t
   const int64_t ab2 = (2 * c->hstage_cap + 255) & ~(int64_t)255;
   const int64_t ab8 = (8 * c->hstage_cap + 255) & ~(int64_t)255;
   ddhf_window dw[kHostGroup];
+  // each window's binning waits only for its own copy, so the first group
+  // starts once its first window is in
   for (int g0 = 0, k = 0; g0 < n_windows; g0 += G, ++k) {
     const int b = k & 1;
     const int ng = std::min(G, n_windows - g0);
@@ -926,15 +943,14 @@ ddhf_status ddhf_detect_batch_host(ddhf_ctx *h, const ddhf_window *wins, int32_t
         DDHF_CUDA_TRY(c, cudaMemcpyAsync(dt, W.t_us, 8 * n, cudaMemcpyHostToDevice, cs));
         DDHF_CUDA_TRY(c, cudaMemcpyAsync(dp, W.p, n, cudaMemcpyHostToDevice, cs));
       }
+      DDHF_CUDA_TRY(c, cudaEventRecord(c->h_win[b * kHostGroup + i], cs));
       dw[i] = W;
       dw[i].x = dx;
       dw[i].y = dy;
       dw[i].t_us = dt;
       dw[i].p = dp;
     }
-    DDHF_CUDA_TRY(c, cudaEventRecord(c->h_ready[b], cs));
-    DDHF_CUDA_TRY(c, cudaStreamWaitEvent(s, c->h_ready[b], 0));
-    DDHF_TRY(run_detect(c, dw, ng, c->hbox, cap, c->hnbox, nullptr, s));
+    DDHF_TRY(run_detect(c, dw, ng, c->hbox, cap, c->hnbox, nullptr, s, &c->h_win[b * kHostGroup]));
     DDHF_CUDA_TRY(c, cudaEventRecord(c->h_free[b], s));
     if (cap > 0)
       DDHF_CUDA_TRY(c, cudaMemcpyAsync(boxes_host + (int64_t)g0 * cap, c->hbox,

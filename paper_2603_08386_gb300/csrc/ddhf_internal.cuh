@@ -194,6 +194,7 @@ struct Ctx {
   int hstage_windows = 0;                // windows per staging set
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t h_ready[2] = {nullptr, nullptr}, h_free[2] = {nullptr, nullptr}, h_start = nullptr;
+  cudaEvent_t h_win[32] = {};  // per staged window (2 sets of up to 16): its copy is done
   ddhf_box *hbox = nullptr;
   int32_t *hnbox = nullptr;
   int64_t hbox_cap = 0;                  // boxes the device box buffer holds
