@@ -328,7 +328,7 @@ __device__ __forceinline__ void store_tile(const BlockedArgs &A, const Acc<TB> &
 }
 
 // Light pixels of one slot, spectra to global memory. A warp takes runs of
-// kRun consecutive active pixels and, when their event lists follow one
+// `run` consecutive active pixels and, when their event lists follow one
 // another in memory (the CSR order of the binning), streams the run's events
 // through the 16-event factor chunks in that order: the factors of an event do
 // not depend on its pixel, so one chunk serves the end of one pixel and the
@@ -336,26 +336,33 @@ __device__ __forceinline__ void store_tile(const BlockedArgs &A, const Acc<TB> &
 // last event is in. Events of pixels outside the run's light set (heavy ones,
 // pixels left to the hybrid path, inactive pixels) are skipped chunk-wise.
 // Runs whose lists are not in order (caller-built lists) are streamed one
-// pixel at a time.
+// pixel at a time. The run length is 16 pixels when there are at least eight
+// such runs per warp of the grid, and halves (down to one pixel) until there
+// are: on a sparse window the warps then share the pixels evenly instead of a
+// few runs of heavy-tailed pixels setting the kernel's time. A pixel's events
+// are accumulated in the same order whatever the run length, so the spectra
+// do not depend on it.
 template <int TB>
 __device__ __forceinline__ void light_stream(const BlockedArgs &A, float4 *stage) {
-  constexpr int kRun = 16;
   const int lane = threadIdx.x & 31;
   const int e = lane & 15;
   const GridConst &g = A.g;
   const SlotView &v = A.views[A.slot0];
   const int64_t n_act = (int64_t)v.counters[2];
   const int rows_per_pass = 4 * TB;
+  const int64_t n_warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  int run = 16;
+  while (run > 1 && (int64_t)run * n_warps * 8 > n_act) run >>= 1;
   for (;;) {
     uint32_t a0 = 0;
-    if (lane == 0) a0 = atomicAdd(&A.cursors[1], (uint32_t)kRun);
+    if (lane == 0) a0 = atomicAdd(&A.cursors[1], (uint32_t)run);
     a0 = __shfl_sync(0xffffffffu, a0, 0);
     if ((int64_t)a0 >= n_act) break;
-    // lane q < kRun: pixel a0 + q of the run, its event range and whether it is light
+    // lane q < run: pixel a0 + q of the run, its event range and whether it is light
     const int64_t aq = (int64_t)a0 + lane;
     uint32_t q_lo = 0, q_hi = 0;
     bool q_ok = false;
-    if (lane < kRun && aq < n_act) {
+    if (lane < run && aq < n_act) {
       const uint32_t key = v.active[aq];
       q_lo = v.offsets[key];
       q_hi = v.offsets[key + 1];
