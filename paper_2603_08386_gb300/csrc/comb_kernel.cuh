@@ -22,22 +22,28 @@ namespace ddhf {
 template <int NW, bool CPLX>
 __global__ void __launch_bounds__(128, NW == 2 ? 6 : (NW == 3 ? 8 : 1)) k_comb(const float *__restrict__ P, int64_t ld, int64_t cap_px,
                        const uint32_t *__restrict__ active, const uint64_t *__restrict__ counters,
-                       CombConst cc, float *log_sf, float *snr, int32_t *f0, uint8_t *mask,
-                       int warp_bytes, int spec_smem, uint32_t *flags) {
+                       unsigned long long *cursor, CombConst cc, float *log_sf, float *snr,
+                       int32_t *f0, uint8_t *mask, int warp_bytes, int spec_smem, uint32_t *flags) {
   extern __shared__ float4 smem4[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned char *base = reinterpret_cast<unsigned char *>(smem4) + warp * warp_bytes;
   float *Pw = reinterpret_cast<float *>(base);
   unsigned char *scratch = base + (spec_smem ? ((cc.N * 4 + 15) & ~15) : 0);
   const int64_t n_active = (int64_t)counters[2];
-  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const bool vec = (ld % (CPLX ? 2 : 4) == 0) && ((reinterpret_cast<uintptr_t>(P) & 15) == 0);
   const int N = cc.N;
   // a row in floats: N powers, or N complex values
   const int64_t ldf = CPLX ? 2 * ld : ld;
   const int row_floats = CPLX ? 2 * N : N;
-  for (int64_t a = wid; a < n_active && a < cap_px; a += nwarps) {
+  // pixels are taken one at a time from a counter that the launcher zeroes
+  // (the cost of a pixel varies with its flatness test and its evaluated
+  // candidates, so warps that drew costly pixels take fewer of them); the
+  // next index is fetched while the current pixel is scored
+  unsigned long long next = 0;
+  if (lane == 0) next = atomicAdd(cursor, 1ull);
+  for (int64_t a = (int64_t)__shfl_sync(0xffffffffu, next, 0); a < n_active && a < cap_px;
+       a = (int64_t)__shfl_sync(0xffffffffu, next, 0)) {
+    if (lane == 0) next = atomicAdd(cursor, 1ull);
     const float *row = P + (CPLX ? (int64_t)active[a] : a) * ldf;
     if (!CPLX && !spec_smem) {
       // a spectrum too large for shared memory is scored where it is
@@ -147,6 +153,10 @@ ddhf_status launch_comb_t(Ctx *c, const float *P, int64_t cap_px, float *log_sf,
   const int warp_bytes = (spec_smem ? spec_b : 0) + scratch_b;
   const size_t smem = (size_t)warp_bytes * wpb;
   DDHF_CUDA_TRY(c, cudaMemsetAsync(mask, 0, c->npx, s));
+  // the pixel counter of this launch: word 6 of the slot's counters (unused
+  // by the binning), so that the combs of different windows never share one
+  unsigned long long *cursor = reinterpret_cast<unsigned long long *>(sl.counters + 6);
+  DDHF_CUDA_TRY(c, cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), s));
 #define DDHF_COMB_CASE(NWV)                                                                    \
   {                                                                                            \
     auto kern = k_comb<NWV, CPLX>;                                                             \
@@ -159,7 +169,7 @@ ddhf_status launch_comb_t(Ctx *c, const float *P, int64_t cap_px, float *log_sf,
       return DDHF_ERR_UNSUPPORTED;                                                             \
     }                                                                                          \
     kern<<<c->num_sms * occ, wpb * 32, smem, s>>>(P, ld > 0 ? ld : c->grid.n_bins, cap_px,     \
-                                                  sl.active, sl.counters, c->comb, log_sf, snr, \
+                                                  sl.active, sl.counters, cursor, c->comb, log_sf, snr, \
                                                   f0, mask, warp_bytes, spec_smem, c->flags);  \
   }
   if (variant == 2) DDHF_COMB_CASE(2)
