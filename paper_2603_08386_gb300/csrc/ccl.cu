@@ -74,12 +74,19 @@ __global__ void k_label_union(const uint8_t *__restrict__ mask, int32_t *lab, in
        i += (int64_t)gridDim.x * blockDim.x) {
     if (!mask[i]) continue;
     const int x = (int)(i % W), y = (int)(i / W);
-    if (x > 0 && mask[i - 1]) unite(lab, (int)i, (int)(i - 1), flags, limit);
-    if (y > 0) {
-      const int64_t up = i - W;
-      if (x > 0 && mask[up - 1]) unite(lab, (int)i, (int)(up - 1), flags, limit);
-      if (mask[up]) unite(lab, (int)i, (int)up, flags, limit);
-      if (x < W - 1 && mask[up + 1]) unite(lab, (int)i, (int)(up + 1), flags, limit);
+    // Only the unions that no other pixel's own unions imply: the pixel above,
+    // when set, is joined to the one left of it and to the one right of it by
+    // their left-neighbour unions, and to this pixel's left neighbour by that
+    // neighbour's up-right union; the left neighbour, when set, is joined to
+    // the pixel above it by its own up union. The components (and so the
+    // minimum-index labels) are those of all eight-neighbour unions.
+    const bool left = x > 0 && mask[i - 1];
+    if (y > 0 && mask[i - W]) {
+      unite(lab, (int)i, (int)(i - W), flags, limit);
+    } else {
+      if (left) unite(lab, (int)i, (int)(i - 1), flags, limit);
+      else if (y > 0 && x > 0 && mask[i - W - 1]) unite(lab, (int)i, (int)(i - W - 1), flags, limit);
+      if (y > 0 && x < W - 1 && mask[i - W + 1]) unite(lab, (int)i, (int)(i - W + 1), flags, limit);
     }
   }
 }
