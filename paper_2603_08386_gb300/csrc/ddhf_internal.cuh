@@ -157,7 +157,9 @@ struct Ctx {
   // work queue of the persistent kernel
   uint64_t *work = nullptr;      // [heavy_cap] heavy items (slot << 32 | active index)
   int64_t heavy_cap = 0;
-  uint32_t *qctl = nullptr;      // [16] queue counters
+  uint32_t *qctl = nullptr;      // [16] queue counters: [0] heavy count, [1-2] spectrum cursors,
+                                 // [4] soft-comb cursor, [8] kept events of a binning, [9]
+                                 // label count, [12-13] hybrid lists, [14] hybrid cursor
   // labelling / boxes scratch
   int32_t *box_root = nullptr;   // [npx]
   int32_t *box_tmp = nullptr;    // [npx * 6]

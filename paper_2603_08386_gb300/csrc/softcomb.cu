@@ -53,16 +53,22 @@ struct SoftArgs {
   uint64_t barrett;        // floor((2^64-1) / 1e9)
   int64_t npx;             // keys at or beyond it are skipped (DDHF_FLAG_INPUT)
   uint32_t *flags;
+  uint32_t *cursor;        // next pixel to take (zeroed before each launch)
 };
 
 template <bool BWD>
 __global__ void __launch_bounds__(256) k_softcomb(SoftArgs A) {
   const int lane = threadIdx.x & 31;
-  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const uint64_t D9 = 1000000000ull;
   const int nq = 2 * A.Q + 1;
-  for (int64_t a = wid; a < A.n_px; a += nwarps) {
+  // pixels are taken one at a time from a counter (a pixel's cost grows with
+  // its events, which are heavy-tailed); the next index is fetched while the
+  // current pixel is processed
+  uint32_t next = 0;
+  if (lane == 0) next = atomicAdd(A.cursor, 1u);
+  for (int64_t a = __shfl_sync(0xffffffffu, next, 0); a < A.n_px;
+       a = __shfl_sync(0xffffffffu, next, 0)) {
+    if (lane == 0) next = atomicAdd(A.cursor, 1u);
     const uint32_t key = A.pixels[a];
     // a key off the sensor has no events: S = 0, zero gradients, flagged
     const bool key_ok = (int64_t)key < A.npx;
@@ -347,6 +353,8 @@ extern "C" ddhf_status ddhf_softcomb(ddhf_ctx *h, int64_t n_px, const uint32_t *
   A.barrett = ~0ull / 1000000000ull;
   A.npx = c->npx;
   A.flags = c->flags;
+  A.cursor = c->qctl + 4;
+  DDHF_CUDA_TRY(c, cudaMemsetAsync(A.cursor, 0, sizeof(uint32_t), s));
   const int blocks = (int)std::min<int64_t>(ceil_div(n_px, 8), (int64_t)c->num_sms * 16);
   if (bwd) {
     k_softcomb<true><<<blocks, 256, 0, s>>>(A);
