@@ -25,7 +25,12 @@
  *    errors. Overflow of a caller-sized output is flagged on the device and
  *    reported as DDHF_ERR_CAPACITY by ddhf_get_stats().
  *  - A context is bound to the CUDA device that was current at ddhf_create()
- *    and must be used from one host thread at a time.
+ *    and must be used from one host thread at a time. Its kernels keep work
+ *    counters in the context's workspace (one set per window slot, plus
+ *    context-wide ones), so calls enqueued on different streams of one
+ *    context must not run on the GPU at the same time; the overlap that
+ *    ddhf_detect_batch arranges itself (the comb of one window beside the
+ *    spectra of the next) uses separate counters.
  */
 #ifndef DDHF_H
 #define DDHF_H
