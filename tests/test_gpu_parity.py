@@ -250,6 +250,49 @@ def test_label_and_boxes_bit_exact(seed, density):
         c.close()
 
 
+def _structured_masks(W, H, rng):
+    yy, xx = np.mgrid[0:H, 0:W]
+    out = {
+        "full": np.ones((H, W), bool),
+        "checkerboard": (xx + yy) % 2 == 0,      # connected through diagonals only
+        "anti-diagonals": (xx + yy) % 3 == 0,    # separate diagonal lines
+        "diagonals": (xx - yy) % 4 == 0,
+        "rows": yy % 2 == 0,
+        "columns": xx % 2 == 0,
+        "staircase": (xx // 2) == (yy % (W // 2)),
+        "single pixels": (xx % 2 == 0) & (yy % 2 == 0),
+        "dense noise": rng.random((H, W)) < 0.6,
+        "sparse noise": rng.random((H, W)) < 0.3,
+    }
+    # a ring with a gap closed only by one diagonal step, and an X
+    ring = np.zeros((H, W), bool)
+    ring[5, 5:40] = ring[30, 5:40] = ring[5:31, 5] = ring[5:31, 39] = True
+    ring[30, 20] = False
+    ring[31, 20] = True
+    x_shape = (np.abs(xx - yy) == 0) | (np.abs(xx + yy - (H - 1)) == 0)
+    out["ring with a diagonal bridge"] = ring
+    out["cross of diagonals"] = x_shape & (xx < H)
+    return out
+
+
+def test_label_structured_masks_bit_exact():
+    # diagonal-only connections and every left / up / up-left / up-right
+    # neighbour pattern, against the oracle's breadth-first labelling
+    W, H = 97, 61
+    rng = np.random.default_rng(11)
+    s = synth.Scene(W=W, H=H, t0=0, window_us=10, x=np.zeros(0, np.int16),
+                    y=np.zeros(0, np.int16), t=np.zeros(0, np.int64), p=np.zeros(0, np.int8),
+                    grid=synth.hz_grid(0, 10, 10))
+    c = ctx_for(s)
+    for name, m in _structured_masks(W, H, rng).items():
+        mask = m.astype(np.uint8).ravel()
+        lab = c.label(torch.from_numpy(mask).cuda())
+        ref, _ = oracle.ccl8(mask, W, H)
+        np.testing.assert_array_equal(lab.cpu().numpy(), ref, err_msg=name)
+    c.stats()
+    c.close()
+
+
 def test_boxes_cap_and_hand_cases():
     W, H = 80, 10
     m = np.zeros((H, W), np.uint8)
