@@ -217,20 +217,24 @@ def slide_leg(wins, W, H, grid, torch, ddhf, hop_us=3750, rebuild_every=64, cap_
         unit="ms per hop (CUDA events); delta terms = (events in + events out) x bins")
 
 
-def latency_sweep(means, W, H, grid, tuning, torch, ddhf, replays=100, seed=1003):
+def latency_sweep(means, W, H, grid, torch, ddhf, replays=100, seed=1003):
     """One 1280x720 window of the C3 recipe at lower event densities (stream 0,
     window 0, the Pareto counts scaled to `mean` events per pixel): the
-    graph-replayed detection timed replay by replay. Gives the largest event
-    count whose median latency is under 1 ms."""
+    graph-replayed detection timed replay by replay, each density with the
+    tuning the autotuner picks on that window (a sparse window gains from other
+    thresholds than the full-density batch: the hybrid route's fixed cost is
+    not repaid by a few heavy pixels). Gives the largest event count whose
+    median latency is under 1 ms."""
+    from paper_2603_08386_gb300 import tune
     rows = []
     for m in means:
         sc = synth.config3_window(0, 0, seed=seed, W=W, H=H, mean_per_px=m)
         c = ddhf.Context(W, H, grid, max_events=max(sc.n, 1), max_windows=1)
-        c.set_tuning(**{k: v for k, v in tuning.items() if k != "how"})
         d = ddhf.events_to_device(sc)
         wl = [(d[0], d[1], d[2], d[3], sc.n, sc.t0, sc.window_us)]
         bx = torch.empty((256, 5), dtype=torch.int32, device="cuda")
         nb = torch.zeros(1, dtype=torch.int32, device="cuda")
+        tun, _ = tune.autotune(c, wl, bx, 256, nb)
         for _ in range(5):
             ddhf.ddhf_detect_batch(c.h, wl, bx, 256, nb, None, use_graph=True)
         torch.cuda.synchronize()
@@ -247,10 +251,10 @@ def latency_sweep(means, W, H, grid, tuning, torch, ddhf, replays=100, seed=1003
         q25, q50, q75, q95 = np.percentile(lt, [25, 50, 75, 95])
         rows.append(dict(mean_per_px=m, events=int(sc.n), active_pixels=int(st["n_active"]),
                          terms=int(st["terms"]), median_ms=float(q50), iqr_ms=float(q75 - q25),
-                         p95_ms=float(q95)))
+                         p95_ms=float(q95), tuning=tun))
     under = [r["events"] for r in rows if r["median_ms"] < 1.0]
     return dict(window=f"{W}x{H}, 30 ms, C3 recipe (stream 0, window 0) at lower densities; "
-                       f"{replays} graph replays each",
+                       f"{replays} graph replays each, autotuned per density",
                 points=rows, largest_events_under_1ms=max(under) if under else None)
 
 
@@ -689,7 +693,7 @@ def main():
     # ------------------------------------------------------------ latency at lower densities
     sweep = None
     if not args.no_sweep and rank == 0:
-        sweep = latency_sweep((1.0, 2.0, 3.0, 5.0, 10.0), W, H, grid, tuning, torch, ddhf,
+        sweep = latency_sweep((1.0, 2.0, 3.0, 5.0, 10.0), W, H, grid, torch, ddhf,
                               replays=args.latency_replays)
     labelled = None
     if lab:
