@@ -43,7 +43,8 @@ struct Slot {
   uint32_t *ev = nullptr;       // [max_events] packed events, pixel-major
   uint32_t *offsets = nullptr;  // [npx + 1]
   uint32_t *active = nullptr;   // [npx] active pixel keys, ascending
-  uint64_t *counters = nullptr; // [8] n_valid, n_dropped, n_active, n_in, n_heavy, terms, -, n_rotor
+  uint64_t *counters = nullptr; // [8] n_valid, n_dropped, n_active, n_in, n_heavy, terms,
+                                // comb pixel cursor, n_rotor
   uint8_t *mask = nullptr;      // [npx] rotor mask
   int32_t *labels = nullptr;    // [npx]
   float *log_sf = nullptr;      // [npx] per active pixel (active-list order)
